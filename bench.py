@@ -1,0 +1,405 @@
+"""Benchmark: ray-segments/s of the column-density trace at 512^3, Nside 1.
+
+Workload: 512^3 uniform leaf grid (134,217,728 leaves, Morton keys), lognormal
+density (P(k) ~ k^-4, sigma 2), 4 FP32 species; sources = every leaf centre;
+12 HEALPix Nside-1 directions (1.61e9 rays); F32-Kahan columns (25.8 GB).
+A step is one full trace of that workload.  Inputs (3.4 GB tree, 3.2 GB
+sources) and output are far larger than L2, so no flush is needed between
+steps.  Also reported: the FP64 form, the adjoint / forward time ratio, an
+end-to-end number with host buffers, and the CPU oracle on a sample.
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+BYTES_PER_SEGMENT = 8 + 1 + 4 * 4  # key + level + 4 FP32 densities (algorithmic)
+NSIDE = 1
+LEVEL = 9
+METRIC = "ray-segments/s at 512^3 Nside=1 (FP32-Kahan vs FP64 @1e-5 rel); adjoint/fwd time"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--level", type=int, default=LEVEL, help="uniform grid level (9 = 512^3)")
+    p.add_argument("--no-extras", action="store_true", help="skip FP64 form, adjoint, e2e, CPU baseline")
+    p.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
+    return p.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            m = json.load(f)
+        return float(m["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_source_sha() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2605_09882_gb300", "csrc")
+    for n in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, n), "rb") as f:
+            h.update(n.encode() + f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
+    """DRAM bytes per launch of the trace kernel from the committed ncu summary,
+    if it was taken from the current kernel sources (else None)."""
+    path = os.path.join(ROOT, "profiles", "trace_f32k_uniform512.json")
+    try:
+        with open(path) as f:
+            m = json.load(f)
+        if m.get("kernel_source_sha") == kernel_source_sha():
+            return float(m["dram_bytes_per_full_launch"])
+    except Exception:
+        pass
+    return None
+
+
+class Clocks:
+    """nvidia-smi samples during the timed region."""
+
+    def __init__(self, index: int):
+        self.path = tempfile.mktemp(suffix=".csv")
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(self.path, "w")
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if not self.p:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.close()
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = max(mx, float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ oracle
+
+def oracle_sample(keys_h, lev_h, dens_h64, n_leaves, seconds, seed=5, level=LEVEL):
+    """Times the oracle on a random sample of sources sized to ~`seconds`."""
+    import oracle
+    import synth
+    rng = np.random.default_rng(seed)
+    dirs = oracle.healpix(NSIDE)
+    nth = os.cpu_count() or 1
+
+    def centres(idx):
+        cl = synth.Cloud(keys_h[idx], lev_h[idx], np.zeros((len(idx), 1)), (1 << 21,) * 3)
+        return synth.leaf_centres(cl)
+
+    def run(n):
+        idx = np.sort(rng.choice(n_leaves, size=n, replace=False))
+        src = centres(idx)
+        t0 = time.perf_counter()
+        cols, _, nseg = oracle.trace(keys_h, lev_h, dens_h64, src, dirs, nthreads=nth)
+        dt = time.perf_counter() - t0
+        return idx, cols, int(nseg.sum()), dt
+
+    _, _, seg0, dt0 = run(256)
+    rate = seg0 / max(dt0, 1e-6)
+    n = int(min(max(256, 256 * seconds / max(dt0, 1e-3)), 400_000))
+    idx, cols, seg, dt = run(n)
+    return {"idx": idx, "cols": cols, "segments": seg, "seconds": dt, "threads": nth, "n_src": n,
+            "rate_small": rate}
+
+
+def cpu_model():
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part")):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
+
+
+# -------------------------------------------------------------- reference
+
+def run_reference(a, rank, world):
+    """The reference arm: the plain FP64 oracle on the host cores, on bounded
+    samples of the same workload, same metric and unit."""
+    if rank != 0:
+        return 0
+    import torch
+    from synth import torchgen
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    keys, lev, dens, _ = torchgen.uniform_cloud(a.level, 2.0, 5, device=dev)
+    keys_h = keys.cpu().numpy().view(np.uint64)
+    lev_h = lev.cpu().numpy()
+    dens_h = dens.cpu().numpy().astype(np.float64)
+    del keys, lev, dens
+    n = keys_h.shape[0]
+    per_step = max(4.0, 60.0 / max(a.steps + a.warmup, 1))
+    for _ in range(a.warmup):
+        oracle_sample(keys_h, lev_h, dens_h, n, per_step / 4, level=a.level)
+    segs, secs, nsrc, th = 0, 0.0, 0, 1
+    for k in range(a.steps):
+        r = oracle_sample(keys_h, lev_h, dens_h, n, per_step, seed=100 + k, level=a.level)
+        segs += r["segments"]
+        secs += r["seconds"]
+        nsrc += r["n_src"]
+        th = r["threads"]
+    v = segs / secs
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "ray-segments/s",
+            "n_gpus": world, "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * secs / a.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": f"{1 << a.level}^3 uniform lognormal cloud (sigma 2, 4 species), "
+                                   "leaf-centre sources, HEALPix Nside 1", "sampled": True},
+            "cpu_baseline": {"value": v, "unit": "ray-segments/s", "cores": th, "kind": "oracle",
+                             "sample": f"{nsrc} random leaf-centre sources x 12 rays over {a.steps} steps "
+                                       f"({segs} segments), CPU {cpu_model()}"},
+            "e2e": {"value": v, "unit": "ray-segments/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------- ours
+
+def main():
+    a = parse()
+    rank, world, local = dist_env()
+    if world > 1 and a.impl == "ours":
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    if a.impl == "reference":
+        return run_reference(a, rank, world)
+
+    import torch
+
+    import paper_2605_09882_gb300 as rt
+    from synth import torchgen
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    L = a.level
+    n_side_cells = 1 << L
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    # ---- inputs, resident in HBM
+    keys, lev, dens, _ = torchgen.uniform_cloud(L, 2.0, 5, device=dev)
+    n = keys.numel()
+    src = torchgen.uniform_centres(L, torch.arange(n, device=dev))
+    tree = rt.Octree(keys, lev)
+    nd = 12 * NSIDE * NSIDE
+    out = torch.empty((n, nd, 4), dtype=torch.float32, device=dev)
+
+    def fwd(mode="f32k", o=None):
+        return rt.trace_columns(tree, src, NSIDE, dens, mode, out=o if o is not None else out)
+
+    for _ in range(a.warmup):
+        fwd()
+    barrier()
+    tree.reset_stats()
+    clocks = Clocks(local)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * a.steps)]
+    barrier()
+    for k in range(a.steps):
+        ev[2 * k].record(stream)
+        fwd()
+        ev[2 * k + 1].record(stream)
+    barrier()
+    clk = clocks.stop()
+    launch_ms = [ev[2 * k].elapsed_time(ev[2 * k + 1]) for k in range(a.steps)]
+    total_ms = ev[0].elapsed_time(ev[-1])
+    st = tree.stats()
+    assert st["status"] == 0, st
+    seg_per_step = st["segments"] // a.steps
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t)
+    value = world * seg_per_step * a.steps / (total_ms / 1e3)
+    avg_launch_s = float(np.mean(launch_ms)) / 1e3
+    peak, peak_kind = peaks()
+    achieved = BYTES_PER_SEGMENT * seg_per_step / avg_launch_s / 1e9
+    traffic = profiled_traffic()
+
+    extras = {}
+    cpu = None
+    e2e = None
+    if not a.no_extras:
+        # ---- FP64 form (same walk, FP64 columns)
+        out64 = torch.empty((n, nd, 4), dtype=torch.float64, device=dev)
+        fwd("fp64", out64)
+        barrier()
+        tree.reset_stats()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fwd("fp64", out64)
+        e1.record(stream)
+        barrier()
+        t64 = e0.elapsed_time(e1) / 1e3
+        s64 = tree.stats()
+        extras["fp64_form"] = {"value": s64["segments"] / t64, "unit": "ray-segments/s",
+                               "ms_per_step": t64 * 1e3}
+        # agreement of the two forms on the full output
+        mx = torch.zeros(4, dtype=torch.float64, device=dev)
+        sm = torch.zeros(4, dtype=torch.float64, device=dev)
+        for c0 in range(0, n, 1 << 22):
+            rel = (out[c0:c0 + (1 << 22)].double() - out64[c0:c0 + (1 << 22)]).abs_()
+            rel /= out64[c0:c0 + (1 << 22)].abs().clamp_min(1e-300)
+            mx = torch.maximum(mx, rel.amax(dim=(0, 1)))
+            sm += rel.sum(dim=(0, 1))
+        extras["f32k_vs_fp64"] = {"max_rel_per_species": [float(x) for x in mx],
+                                  "mean_rel_per_species": [float(x) / (n * nd) for x in sm]}
+        del rel, out64
+        torch.cuda.empty_cache()
+        # ---- adjoint (F32-Kahan walk, FP64 gradient), seed = the forward output
+        grad = torch.zeros((n, 4), dtype=torch.float64, device=dev)
+        rt.trace_columns_adjoint(tree, src, NSIDE, out, "f32k", grad_dens=grad)
+        barrier()
+        e0.record(stream)
+        rt.trace_columns_adjoint(tree, src, NSIDE, out, "f32k", grad_dens=grad)
+        e1.record(stream)
+        barrier()
+        tadj = e0.elapsed_time(e1) / 1e3
+        extras["adjoint"] = {"ms_per_step": tadj * 1e3, "adjoint_over_forward": tadj / avg_launch_s}
+        del grad
+        torch.cuda.empty_cache()
+        # ---- CPU oracle on a sample (rank 0, N = 1) + parity of those outputs
+        keys_h = keys.cpu().numpy().view(np.uint64)
+        lev_h = lev.cpu().numpy()
+        if rank == 0 and world == 1:
+            dens_h64 = dens.cpu().numpy().astype(np.float64)
+            r = oracle_sample(keys_h, lev_h, dens_h64, n, a.cpu_seconds)
+            got = out[torch.from_numpy(r["idx"]).to(dev)].double().cpu().numpy()
+            err = np.abs(got - r["cols"]) / np.maximum(np.abs(r["cols"]), 1e-300)
+            cpu = {"value": r["segments"] / r["seconds"], "unit": "ray-segments/s", "cores": r["threads"],
+                   "kind": "oracle",
+                   "sample": f"{r['n_src']} random leaf-centre sources x 12 rays ({r['segments']} segments), "
+                             f"CPU {cpu_model()}"}
+            extras["parity_sample"] = {"n_src": r["n_src"], "max_rel": float(err.max()),
+                                       "max_rel_per_species": [float(x) for x in err.max(axis=(0, 1))],
+                                       "mean_rel_per_species": [float(x) for x in err.mean(axis=(0, 1))]}
+            del dens_h64
+        # ---- end to end through the public API with host buffers
+        keys_p = torch.from_numpy(keys_h.view(np.int64)).pin_memory()
+        lev_p = torch.from_numpy(lev_h).pin_memory()
+        dens_p = dens.cpu().pin_memory()
+        src_p = src.cpu().pin_memory()
+        out_p = torch.empty((n, nd, 4), dtype=torch.float32).pin_memory()
+        del tree
+        h2d = sum(t.numel() * t.element_size() for t in (keys_p, lev_p, dens_p, src_p))
+        d2h = out_p.numel() * out_p.element_size()
+        e2e_steps = 2
+        barrier()
+        t0 = time.perf_counter()
+        e0.record(stream)
+        for _ in range(e2e_steps):
+            kd = keys_p.to(dev, non_blocking=True)
+            ld = lev_p.to(dev, non_blocking=True)
+            dd = dens_p.to(dev, non_blocking=True)
+            sd = src_p.to(dev, non_blocking=True)
+            t2 = rt.Octree(kd, ld)
+            rt.trace_columns(t2, sd, NSIDE, dd, "f32k", out=out)
+            out_p.copy_(out, non_blocking=True)
+            torch.cuda.synchronize()
+            t2.close()
+        e1.record(stream)
+        barrier()
+        wall = time.perf_counter() - t0
+        e2e = {"value": world * seg_per_step * e2e_steps / wall, "unit": "ray-segments/s",
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+               "ms_per_step": wall * 1e3 / e2e_steps}
+
+    line = {
+        "metric": METRIC,
+        "value": value,
+        "unit": "ray-segments/s",
+        "n_gpus": world,
+        "steps": a.steps,
+        "warmup": a.warmup,
+        "ms_per_step": total_ms / a.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": f"{n_side_cells}^3 uniform lognormal cloud (P(k)~k^-4, sigma 2), 4 FP32 species, "
+                               f"all {n} leaf-centre sources, HEALPix Nside 1 ({n * nd} rays), F32-Kahan columns",
+                   "segments_per_step": seg_per_step, "l2": "inputs and output larger than L2 (no flush)",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "peak_kind": peak_kind,
+                     "bytes_per_segment": BYTES_PER_SEGMENT, "kernel": "k_trace<fwd, F32K, uniform, S=4>"},
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "clocks": clk,
+        "gpu_launches": a.steps,
+    }
+    line.update(extras)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,179 @@
+/*
+ * rt_api.h - C ABI of the GB300 column-density tracer.
+ *
+ * The library computes, for every source point p and every HEALPix direction
+ * q, the per-species column densities I(p,q,k) = sum_j n_k[j] * r_cell,j
+ * (arXiv 2605.09882, Sec. 2.2, equation for I(p,q)) by reverse ray tracing
+ * through a leaf-only linear octree: a DDA walk from cell boundary to cell
+ * boundary, a Morton-code lookup of the next leaf in the sorted key array
+ * (Sec. 2.2.1) and the slab method for each chord r_cell = t_out - t_in
+ * (Sec. 2.2.2).  The adjoint (the transpose of that linear map) is an
+ * addition of this library; the paper has no gradient.
+ *
+ * Conventions shared by every entry point:
+ *  - Domain: the unit cube [0,1)^3, or the box [0, extent_b * 2^-21) when an
+ *    extent is given.  Integer positions use the depth-21 lattice.
+ *  - Octree: n_leaves keys (uint64) sorted strictly ascending and levels
+ *    (uint8, 0..21).  Leaf j covers the Morton interval
+ *    [key_j, key_j + 8^(21 - level_j)); key = interleave(x, y, z) of its
+ *    depth-21 integer corner with x in bit 3b, y in bit 3b+1, z in bit 3b+2.
+ *    The leaves must tile the domain box exactly.
+ *  - Densities: [n_leaves][n_species] row-major, species fastest, RT_F32 or
+ *    RT_F64.
+ *  - Sources: float64 [n_src][3].  Each coordinate is truncated to the 2^-53
+ *    lattice (a move below 1.2e-16 box lengths) so that every face-minus-
+ *    source difference is exact in FP64.
+ *  - Directions: the 12 * nside^2 HEALPix pixel centres in RING order
+ *    (nside a power of two, 1..1024), as returned by rt_healpix_dirs.
+ *  - Output columns: [n_src][12 * nside^2][n_species], species fastest, in
+ *    units of (density) x (box length).
+ *  - Pointers named d_* are device memory owned by the caller; h_* are host
+ *    memory owned by the caller.  Nothing is freed or retained by a call except
+ *    where stated.
+ *  - Streams: every device operation is enqueued on `stream` (a cudaStream_t;
+ *    NULL = legacy default stream) and returns before it completes.  Argument
+ *    errors are returned synchronously.  Faults found by a kernel (a source
+ *    outside the domain, a step cap reached, a failed lookup) are recorded in
+ *    the octree's status word, read by rt_get_stats.
+ *  - Threads: calls that share one rt_octree must be ordered on one stream;
+ *    the handle holds the work-queue counter and the statistics.
+ */
+#ifndef RT_API_H
+#define RT_API_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes returned by every int-valued entry point. */
+enum rt_status {
+    RT_OK = 0,
+    RT_ERR_ARG = 1,             /* bad argument (null pointer, size, level > 21, bad nside, ...) */
+    RT_ERR_UNSORTED = 2,        /* keys not strictly ascending */
+    RT_ERR_MISALIGNED = 3,      /* key not a multiple of 8^(21 - level), or bit 63 set */
+    RT_ERR_OVERLAP_OR_GAP = 4,  /* leaves overlap, leave the domain box, or leave a gap */
+    RT_ERR_SOURCE_OUTSIDE = 5,  /* a source coordinate is not finite or outside the domain */
+    RT_ERR_STEP_LIMIT = 6,      /* a ray reached the step cap (never for a valid octree) */
+    RT_ERR_NONFINITE = 7,       /* reserved */
+    RT_ERR_CUDA = 8,            /* a CUDA runtime call failed; see rt_last_error */
+    RT_ERR_OOM = 9,             /* device allocation failed */
+    RT_ERR_LOOKUP_MISS = 10     /* a walked position matched no leaf (never for a valid octree) */
+};
+
+enum rt_dtype { RT_F32 = 0, RT_F64 = 1 };
+
+/* Arithmetic of the walk and of the columns.
+ *  RT_MODE_FP64: every exit time, segment and column in IEEE FP64 without
+ *    contraction; columns are bitwise those of the plain FP64 definition.
+ *  RT_MODE_F32_KAHAN: exit-axis and next-leaf decisions certified equal to the
+ *    FP64 ones (FP32 with an error bound, FP64 only for near-ties), segment
+ *    lengths from double-float times, columns in FP32 with Kahan compensation.
+ *  Visited-leaf sequences are identical in both modes. */
+enum rt_mode { RT_MODE_FP64 = 0, RT_MODE_F32_KAHAN = 1 };
+
+typedef struct rt_octree rt_octree; /* opaque */
+
+/* Statistics and device status accumulated by the calls on one octree. */
+typedef struct rt_stats {
+    uint64_t rays;            /* rays traced */
+    uint64_t segments;        /* (ray, leaf) pairs visited, ties counted once */
+    uint64_t exit_fallbacks;  /* F32-Kahan steps whose exit axis needed FP64 */
+    uint64_t lookup_fallbacks;/* F32-Kahan steps whose next leaf needed FP64 */
+    int32_t status;           /* first device fault (rt_status), RT_OK if none */
+    int32_t reserved;
+    int64_t fault_ray;        /* ray index (s * n_dirs + q) of that fault, -1 if none */
+} rt_stats;
+
+/* Builds the lookup structures of a leaf-only linear octree (Sec. 2.2.1:
+ * leaves stored as compact arrays of Morton code and refinement level).
+ *   d_keys, d_levels: device arrays of n_leaves entries, BORROWED: they must
+ *     stay allocated and unchanged until rt_destroy_octree.
+ *   n_leaves: 1 .. 2^32 - 1.
+ *   h_extent: host int32[3], domain size in depth-21 cells per axis
+ *     (1 .. 2^21), or NULL for the full cube (2^21 each).
+ *   stream: the stream the checks and the table build are enqueued on.
+ *   out: receives the handle on RT_OK, NULL otherwise.
+ * Checks the octree on the device (sorted, aligned, tiling the box; fault
+ * precedence ARG > MISALIGNED > UNSORTED > OVERLAP_OR_GAP), builds a coarse
+ * Morton table over the top levels and synchronizes `stream` once to read the
+ * verdict.  The handle owns the table and a small scratch block. */
+int rt_build_octree(const uint64_t* d_keys, const uint8_t* d_levels, int64_t n_leaves,
+                    const int32_t* h_extent, void* stream, rt_octree** out);
+
+/* Frees a handle and what it owns (not the borrowed keys and levels).
+ * Synchronizes the device first.  NULL is ignored. */
+void rt_destroy_octree(rt_octree* tree);
+
+/* HEALPix pixel centres in RING order (the paper's N_rays = 12 * 4^l
+ * directions, Sec. 2), Gorski et al. 2005 ring equations, evaluated on the
+ * host.  h_out: host float64 [12 * nside^2][3].  Host-only; needs no GPU. */
+int rt_healpix_dirs(int nside, double* h_out);
+
+/* Forward trace (Sec. 2.2, I(p,q) = sum_k f_k r_cell,k, for every source and
+ * direction).
+ *   d_src: float64 [n_src][3] inside the domain box.
+ *   d_dens: [n_leaves][n_species] of dens_dtype; n_species 1..8.
+ *   mode: rt_mode.  d_out: [n_src][12 nside^2][n_species], float32 for
+ *     RT_MODE_F32_KAHAN, float64 for RT_MODE_FP64; fully written (rays from a
+ *     source outside the domain get zeros and set RT_ERR_SOURCE_OUTSIDE).
+ * The first call for a given nside on a device uploads its direction table
+ * (an allocation); make that call outside CUDA graph capture. */
+int rt_trace_columns(const rt_octree* tree, const double* d_src, int64_t n_src, int nside,
+                     const void* d_dens, int n_species, int dens_dtype, int mode,
+                     void* d_out, void* stream);
+
+/* Per-ray path fingerprints: the number of segments and the hash
+ * h <- (h XOR leaf) * 0x100000001b3 (h0 = 0xcbf29ce484222325) over the
+ * visited leaf indices in walk order, for every ray of the walk that
+ * rt_trace_columns does in the same mode.  d_nseg: uint32 [n_src][n_dirs];
+ * d_hash: uint64 [n_src][n_dirs]; either may be NULL. */
+int rt_trace_paths(const rt_octree* tree, const double* d_src, int64_t n_src, int nside,
+                   int mode, uint32_t* d_nseg, uint64_t* d_hash, void* stream);
+
+/* Adjoint of rt_trace_columns with respect to the densities (not in the
+ * paper): d_grad_dens[j,k] += sum over rays (s,q) crossing leaf j of
+ * d_grad_out[s,q,k] * ds(s,q,j).
+ *   d_grad_out: same shape as the forward output; float32 for
+ *     RT_MODE_F32_KAHAN, float64 for RT_MODE_FP64.
+ *   d_grad_dens: float64 [n_leaves][n_species], ACCUMULATED into (the caller
+ *     zeroes it); summation order across rays is not fixed.
+ *   path_policy: 0 = automatic, 1 = recompute the paths (the only policy
+ *     implemented; 2 = record is rejected with RT_ERR_ARG). */
+int rt_trace_columns_adjoint(const rt_octree* tree, const double* d_src, int64_t n_src,
+                             int nside, const void* d_grad_out, int n_species, int mode,
+                             double* d_grad_dens, int path_policy, void* stream);
+
+/* Copies the statistics of `tree` into *h_out after synchronizing `stream`. */
+int rt_get_stats(const rt_octree* tree, rt_stats* h_out, void* stream);
+
+/* Zeroes the statistics and the status word (enqueued on `stream`). */
+int rt_reset_stats(rt_octree* tree, void* stream);
+
+/* Test knob: per-ray step cap (0 restores the geometric bound 3 * 2^lmax + 3,
+ * which no valid walk can reach).  A ray that reaches the cap stops and sets
+ * RT_ERR_STEP_LIMIT instead of looping. */
+int rt_set_step_cap(rt_octree* tree, int64_t cap);
+
+/* Launch shape of the persistent trace kernels: threads per block (a
+ * multiple of 32, 32..1024; 0 = default 256) and resident blocks per SM (0 =
+ * as many as fit).  Applies to later calls in this process. */
+int rt_set_launch(int threads_per_block, int blocks_per_sm);
+
+/* Lookup choice: 1 (default) lets a full cube of equal-level leaves use the
+ * O(1) Morton index; 0 forces the coarse table and key search even then
+ * (both give identical results). */
+int rt_set_lookup(rt_octree* tree, int use_uniform_index);
+
+/* Number of leaves and the deepest level of a handle (host values). */
+int rt_octree_info(const rt_octree* tree, int64_t* n_leaves, int* max_level, int* uniform_level);
+
+/* Message of the last failed call on this host thread ("" if none). */
+const char* rt_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RT_API_H */

@@ -1,0 +1,238 @@
+"""GB300 column-density tracer (RAYTHEIA hot path, arXiv 2605.09882).
+
+Thin ctypes binding over the C ABI in include/rt_api.h.  PyTorch supplies
+device memory and streams only: every step of the trace runs in the library's
+CUDA kernels.  There is no CPU fallback: importing this package without the
+built library raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import _build
+
+__all__ = ["Octree", "healpix_dirs", "trace_columns", "trace_paths", "trace_columns_adjoint",
+           "Columns", "RTError", "MODE_FP64", "MODE_F32_KAHAN", "set_launch", "lib_path"]
+
+MODE_FP64, MODE_F32_KAHAN = 0, 1
+F32, F64 = 0, 1
+STATUS = {0: "RT_OK", 1: "RT_ERR_ARG", 2: "RT_ERR_UNSORTED", 3: "RT_ERR_MISALIGNED",
+          4: "RT_ERR_OVERLAP_OR_GAP", 5: "RT_ERR_SOURCE_OUTSIDE", 6: "RT_ERR_STEP_LIMIT",
+          7: "RT_ERR_NONFINITE", 8: "RT_ERR_CUDA", 9: "RT_ERR_OOM", 10: "RT_ERR_LOOKUP_MISS"}
+
+
+class RTError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Stats(C.Structure):
+    _fields_ = [("rays", C.c_uint64), ("segments", C.c_uint64), ("exit_fallbacks", C.c_uint64),
+                ("lookup_fallbacks", C.c_uint64), ("status", C.c_int32), ("reserved", C.c_int32),
+                ("fault_ray", C.c_int64)]
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def _load():
+    path = _build.LIB
+    if not os.path.exists(path):
+        raise ImportError(f"the CUDA library {path} is not built; run "
+                          "`python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = C.CDLL(path)
+    P, i64, i32 = C.c_void_p, C.c_int64, C.c_int
+    lib.rt_build_octree.argtypes = [P, P, i64, P, P, C.POINTER(P)]
+    lib.rt_destroy_octree.argtypes = [P]
+    lib.rt_destroy_octree.restype = None
+    lib.rt_healpix_dirs.argtypes = [i32, P]
+    lib.rt_trace_columns.argtypes = [P, P, i64, i32, P, i32, i32, i32, P, P]
+    lib.rt_trace_paths.argtypes = [P, P, i64, i32, i32, P, P, P]
+    lib.rt_trace_columns_adjoint.argtypes = [P, P, i64, i32, P, i32, i32, P, i32, P]
+    lib.rt_get_stats.argtypes = [P, C.POINTER(Stats), P]
+    lib.rt_reset_stats.argtypes = [P, P]
+    lib.rt_set_step_cap.argtypes = [P, i64]
+    lib.rt_set_launch.argtypes = [i32, i32]
+    lib.rt_set_lookup.argtypes = [P, i32]
+    lib.rt_octree_info.argtypes = [P, C.POINTER(i64), C.POINTER(i32), C.POINTER(i32)]
+    lib.rt_last_error.restype = C.c_char_p
+    return lib
+
+
+_lib = _load()
+
+
+def _check(code: int):
+    if code != 0:
+        raise RTError(code, _lib.rt_last_error().decode())
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def _dptr(t):
+    return C.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def healpix_dirs(nside: int) -> np.ndarray:
+    """HEALPix pixel centres (RING order) as float64 [12 nside^2][3] (host)."""
+    out = np.zeros((12 * nside * nside, 3), dtype=np.float64)
+    _check(_lib.rt_healpix_dirs(int(nside), out.ctypes.data_as(C.c_void_p)))
+    return out
+
+
+def set_launch(threads_per_block: int = 0, blocks_per_sm: int = 0):
+    _check(_lib.rt_set_launch(int(threads_per_block), int(blocks_per_sm)))
+
+
+class Octree:
+    """Handle over device-resident sorted Morton keys (int64/uint64) and
+    levels (uint8); the tensors are borrowed and kept alive by the handle."""
+
+    def __init__(self, keys, levels, extent=None, stream=None):
+        import torch
+        if keys.device.type != "cuda" or levels.device.type != "cuda":
+            raise ValueError("keys and levels must be CUDA tensors")
+        if keys.dtype not in (torch.int64, torch.uint64) or levels.dtype != torch.uint8:
+            raise ValueError("keys must be int64/uint64 and levels uint8")
+        self.keys = keys.contiguous()
+        self.levels = levels.contiguous()
+        self.n_leaves = int(self.keys.numel())
+        ext = None
+        if extent is not None:
+            ext = (C.c_int32 * 3)(*[int(e) for e in extent])
+        h = C.c_void_p()
+        _check(_lib.rt_build_octree(_dptr(self.keys), _dptr(self.levels), self.n_leaves, ext,
+                                    _stream(stream), C.byref(h)))
+        self._h = h
+        n, lm, ul = C.c_int64(), C.c_int32(), C.c_int32()
+        _check(_lib.rt_octree_info(self._h, C.byref(n), C.byref(lm), C.byref(ul)))
+        self.max_level, self.uniform_level = lm.value, ul.value
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.rt_destroy_octree(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def stats(self, stream=None) -> dict:
+        s = Stats()
+        _check(_lib.rt_get_stats(self._h, C.byref(s), _stream(stream)))
+        return {f: getattr(s, f) for f, _ in Stats._fields_ if f != "reserved"}
+
+    def reset_stats(self, stream=None):
+        _check(_lib.rt_reset_stats(self._h, _stream(stream)))
+
+    def set_step_cap(self, cap: int):
+        _check(_lib.rt_set_step_cap(self._h, int(cap)))
+
+    def set_lookup(self, use_uniform_index: bool):
+        _check(_lib.rt_set_lookup(self._h, 1 if use_uniform_index else 0))
+
+
+def _mode(mode) -> int:
+    if mode in (MODE_FP64, "fp64"):
+        return MODE_FP64
+    if mode in (MODE_F32_KAHAN, "f32k", "f32_kahan"):
+        return MODE_F32_KAHAN
+    raise ValueError(f"unknown mode {mode!r}")
+
+
+def _check_src(src):
+    import torch
+    if src.device.type != "cuda" or src.dtype != torch.float64 or src.dim() != 2 or src.shape[1] != 3:
+        raise ValueError("sources must be a CUDA float64 tensor of shape [n_src, 3]")
+    return src.contiguous()
+
+
+def trace_columns(tree: Octree, src, nside: int, dens, mode="f32k", out=None, stream=None):
+    """Columns [n_src][12 nside^2][S]: float32 (F32-Kahan) or float64 (FP64)."""
+    import torch
+    m = _mode(mode)
+    src = _check_src(src)
+    dens = dens.contiguous()
+    if dens.dim() == 1:
+        dens = dens[:, None]
+    if dens.dtype not in (torch.float32, torch.float64) or dens.shape[0] != tree.n_leaves:
+        raise ValueError("dens must be float32/float64 [n_leaves, S]")
+    S = int(dens.shape[1])
+    nd = 12 * nside * nside
+    odt = torch.float32 if m == MODE_F32_KAHAN else torch.float64
+    if out is None:
+        out = torch.empty((src.shape[0], nd, S), dtype=odt, device=src.device)
+    elif out.dtype != odt or tuple(out.shape) != (src.shape[0], nd, S) or not out.is_contiguous():
+        raise ValueError("out has the wrong dtype, shape or layout")
+    _check(_lib.rt_trace_columns(tree.handle, _dptr(src), int(src.shape[0]), int(nside), _dptr(dens), S,
+                                 F64 if dens.dtype == torch.float64 else F32, m, _dptr(out),
+                                 _stream(stream)))
+    return out
+
+
+def trace_paths(tree: Octree, src, nside: int, mode="f32k", stream=None):
+    """Per-ray segment counts (int32) and path hashes (int64 bits of uint64)."""
+    import torch
+    m = _mode(mode)
+    src = _check_src(src)
+    nd = 12 * nside * nside
+    nseg = torch.empty((src.shape[0], nd), dtype=torch.int32, device=src.device)
+    hsh = torch.empty((src.shape[0], nd), dtype=torch.int64, device=src.device)
+    _check(_lib.rt_trace_paths(tree.handle, _dptr(src), int(src.shape[0]), int(nside), m,
+                               _dptr(nseg), _dptr(hsh), _stream(stream)))
+    return nseg, hsh
+
+
+def trace_columns_adjoint(tree: Octree, src, nside: int, grad_out, mode="f32k", grad_dens=None,
+                          stream=None):
+    """grad_dens[j,k] += sum over rays of grad_out[s,q,k] * ds(s,q,j) (float64)."""
+    import torch
+    m = _mode(mode)
+    src = _check_src(src)
+    gdt = torch.float32 if m == MODE_F32_KAHAN else torch.float64
+    grad_out = grad_out.to(gdt).contiguous()
+    S = int(grad_out.shape[-1])
+    if grad_dens is None:
+        grad_dens = torch.zeros((tree.n_leaves, S), dtype=torch.float64, device=src.device)
+    _check(_lib.rt_trace_columns_adjoint(tree.handle, _dptr(src), int(src.shape[0]), int(nside),
+                                         _dptr(grad_out), S, m, _dptr(grad_dens), 1, _stream(stream)))
+    return grad_dens
+
+
+try:
+    import torch as _torch
+
+    class Columns(_torch.autograd.Function):
+        """Differentiable columns: forward = trace_columns, backward = the
+        adjoint trace (gradient with respect to the per-leaf densities)."""
+
+        @staticmethod
+        def forward(ctx, dens, tree, src, nside, mode="f32k"):
+            ctx.tree, ctx.nside, ctx.mode = tree, nside, mode
+            ctx.save_for_backward(src)
+            ctx.dens_dtype = dens.dtype
+            return trace_columns(tree, src, nside, dens.detach(), mode)
+
+        @staticmethod
+        def backward(ctx, g):
+            (src,) = ctx.saved_tensors
+            gd = trace_columns_adjoint(ctx.tree, src, ctx.nside, g, ctx.mode)
+            return gd.to(ctx.dens_dtype), None, None, None, None
+except ImportError:  # pragma: no cover - torch is required for device memory
+    Columns = None

@@ -1,0 +1,308 @@
+// Public C ABI: argument checks, direction tables, launches, statistics.
+#include <stdio.h>
+#include <stdlib.h>
+
+#include <mutex>
+#include <string>
+
+#include "rt_host.h"
+
+namespace rt {
+
+static thread_local std::string g_err;
+
+int set_error(int code, const char* msg)
+{
+    g_err = msg;
+    return code;
+}
+
+int cuda_error(const char* where)
+{
+    const cudaError_t e = cudaGetLastError();
+    char buf[512];
+    snprintf(buf, sizeof buf, "%s: %s", where, cudaGetErrorString(e));
+    g_err = buf;
+    return (e == cudaErrorMemoryAllocation) ? RT_ERR_OOM : RT_ERR_CUDA;
+}
+
+void clear_error() { g_err.clear(); }
+
+// ----------------------------------------------------------- launch shape
+
+static int g_block = 256;
+static int g_blocks_per_sm = 0;
+
+struct DeviceInfo {
+    int sms = 0;
+};
+static std::mutex g_mu;
+static DeviceInfo g_dev[64];
+static DirConst* g_dirs[64][11];  // per device, per log2(nside); never freed
+
+static int sm_count(int dev)
+{
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (dev < 0 || dev >= 64) return 0;
+    if (!g_dev[dev].sms) cudaDeviceGetAttribute(&g_dev[dev].sms, cudaDevAttrMultiProcessorCount, dev);
+    return g_dev[dev].sms;
+}
+
+static int ilog2_pow2(int v)
+{
+    int l = 0;
+    while ((1 << l) < v) l++;
+    return ((1 << l) == v) ? l : -1;
+}
+
+// Per-direction constants of the HEALPix table for nside, in device memory
+// (uploaded on first use per device, kept until process exit).
+static const DirConst* dir_table(int dev, int nside, int* status)
+{
+    const int l = ilog2_pow2(nside);
+    if (nside < 1 || nside > 1024 || l < 0) {
+        *status = set_error(RT_ERR_ARG, "nside must be a power of two in [1, 1024]");
+        return nullptr;
+    }
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (dev < 0 || dev >= 64) {
+        *status = set_error(RT_ERR_ARG, "device index out of range");
+        return nullptr;
+    }
+    if (g_dirs[dev][l]) return g_dirs[dev][l];
+    const int nd = 12 * nside * nside;
+    double* m = (double*)malloc(sizeof(double) * 3 * nd);
+    DirConst* h = (DirConst*)calloc(nd, sizeof(DirConst));
+    rt_healpix_dirs(nside, m);
+    for (int q = 0; q < nd; q++) {
+        DirConst& d = h[q];
+        d.flags = 0;
+        for (int b = 0; b < 3; b++) {
+            const double v = m[3 * q + b];
+            d.m[b] = v;
+            d.m32[b] = (float)v;
+            if (v != 0.0) {
+                d.inv[b] = 1.0 / v;
+                d.ih[b] = (float)d.inv[b];
+                d.il[b] = (float)(d.inv[b] - (double)d.ih[b]);
+                d.flags |= 1 << b;
+                if (v > 0.0) d.flags |= 8 << b;
+            } else {
+                d.inv[b] = 0.0;
+                d.ih[b] = d.il[b] = 0.f;
+            }
+        }
+        const int pa[3] = {0, 0, 1}, pb[3] = {1, 2, 2};
+        for (int k = 0; k < 3; k++)
+            if ((d.flags & (1 << pa[k])) && (d.flags & (1 << pb[k])) && fabs(d.inv[pa[k]]) == fabs(d.inv[pb[k]]))
+                d.flags |= 1 << (6 + k);
+    }
+    DirConst* dptr = nullptr;
+    if (cudaMalloc(&dptr, sizeof(DirConst) * nd) != cudaSuccess ||
+        cudaMemcpy(dptr, h, sizeof(DirConst) * nd, cudaMemcpyHostToDevice) != cudaSuccess) {
+        *status = cuda_error("direction table upload");
+        if (dptr) cudaFree(dptr);
+        dptr = nullptr;
+    } else {
+        g_dirs[dev][l] = dptr;
+    }
+    free(m);
+    free(h);
+    return dptr;
+}
+
+static bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+// Common argument handling of the trace entry points.
+static int prepare(const rt_octree* t, const double* d_src, int64_t n_src, int nside, int S,
+                   int mode, TraceArgs& a, const char* who)
+{
+    char buf[256];
+    if (!t) {
+        snprintf(buf, sizeof buf, "%s: null octree", who);
+        return set_error(RT_ERR_ARG, buf);
+    }
+    if (n_src < 0 || (n_src > 0 && !d_src)) {
+        snprintf(buf, sizeof buf, "%s: bad sources", who);
+        return set_error(RT_ERR_ARG, buf);
+    }
+    if (S < 1 || S > kMaxSpecies) {
+        snprintf(buf, sizeof buf, "%s: n_species must be in [1, %d]", who, kMaxSpecies);
+        return set_error(RT_ERR_ARG, buf);
+    }
+    if (mode != RT_MODE_FP64 && mode != RT_MODE_F32_KAHAN) {
+        snprintf(buf, sizeof buf, "%s: unknown mode", who);
+        return set_error(RT_ERR_ARG, buf);
+    }
+    int status = RT_OK;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev != t->device) return set_error(RT_ERR_ARG, "octree was built on another device");
+    const DirConst* dirs = dir_table(dev, nside, &status);
+    if (!dirs) return status;
+    memset(&a, 0, sizeof a);
+    a.t = t->dev;
+    if (!t->uniform_allowed) a.t.uniform_level = -1;
+    a.dirs = dirs;
+    a.nd = 12 * nside * nside;
+    a.src = d_src;
+    a.n_src = n_src;
+    a.n_src_pad = (n_src + 31) / 32 * 32;
+    a.S = S;
+    a.st = t->st;
+    return RT_OK;
+}
+
+static int grid_for(int blocks_per_sm_fit)
+{
+    int dev = 0;
+    cudaGetDevice(&dev);
+    int bps = g_blocks_per_sm > 0 ? std::min(g_blocks_per_sm, blocks_per_sm_fit) : blocks_per_sm_fit;
+    if (bps < 1) bps = 1;
+    return sm_count(dev) * bps;
+}
+
+}  // namespace rt
+
+using namespace rt;
+
+extern "C" {
+
+const char* rt_last_error(void) { return g_err.c_str(); }
+
+void rt_destroy_octree(rt_octree* t)
+{
+    if (!t) return;
+    cudaDeviceSynchronize();
+    if (t->table) cudaFree(t->table);
+    if (t->st) cudaFree(t->st);
+    free(t);
+}
+
+int rt_set_launch(int threads_per_block, int blocks_per_sm)
+{
+    if (threads_per_block == 0) threads_per_block = 256;
+    if (threads_per_block < 32 || threads_per_block > 256 || threads_per_block % 32)
+        return set_error(RT_ERR_ARG, "rt_set_launch: threads_per_block must be a multiple of 32 in [32, 256]");
+    if (blocks_per_sm < 0) return set_error(RT_ERR_ARG, "rt_set_launch: blocks_per_sm < 0");
+    g_block = threads_per_block;
+    g_blocks_per_sm = blocks_per_sm;
+    return RT_OK;
+}
+
+int rt_set_step_cap(rt_octree* t, int64_t cap)
+{
+    if (!t || cap < 0) return set_error(RT_ERR_ARG, "rt_set_step_cap: bad argument");
+    t->dev.step_cap = cap ? cap : t->default_cap;
+    return RT_OK;
+}
+
+int rt_set_lookup(rt_octree* t, int use_uniform_index)
+{
+    if (!t) return set_error(RT_ERR_ARG, "rt_set_lookup: null octree");
+    t->uniform_allowed = use_uniform_index ? 1 : 0;
+    return RT_OK;
+}
+
+int rt_octree_info(const rt_octree* t, int64_t* n_leaves, int* max_level, int* uniform_level)
+{
+    if (!t) return set_error(RT_ERR_ARG, "rt_octree_info: null octree");
+    if (n_leaves) *n_leaves = t->dev.n;
+    if (max_level) *max_level = t->dev.lmax;
+    if (uniform_level) *uniform_level = t->dev.uniform_level;
+    return RT_OK;
+}
+
+int rt_trace_columns(const rt_octree* t, const double* d_src, int64_t n_src, int nside,
+                     const void* d_dens, int n_species, int dens_dtype, int mode, void* d_out,
+                     void* stream)
+{
+    TraceArgs a;
+    int st = prepare(t, d_src, n_src, nside, n_species, mode, a, "rt_trace_columns");
+    if (st != RT_OK) return st;
+    if (dens_dtype != RT_F32 && dens_dtype != RT_F64) return set_error(RT_ERR_ARG, "rt_trace_columns: bad dens_dtype");
+    if (n_src == 0) return RT_OK;
+    if (!d_dens || !d_out) return set_error(RT_ERR_ARG, "rt_trace_columns: null densities or output");
+    if (!aligned16(d_dens) || !aligned16(d_out))
+        return set_error(RT_ERR_ARG, "rt_trace_columns: densities and output must be 16-byte aligned");
+    a.dens = d_dens;
+    a.dens_f64 = dens_dtype == RT_F64;
+    a.out = d_out;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int fit = occupancy_fwd(0, mode, n_species, a.t.uniform_level >= 0, g_block);
+    if (cudaMemsetAsync(&t->st->queue, 0, sizeof(unsigned long long), s) != cudaSuccess)
+        return cuda_error("rt_trace_columns: queue reset");
+    if (launch_forward(a, mode, g_block, grid_for(fit), s) != cudaSuccess)
+        return cuda_error("rt_trace_columns: launch");
+    return RT_OK;
+}
+
+int rt_trace_paths(const rt_octree* t, const double* d_src, int64_t n_src, int nside, int mode,
+                   uint32_t* d_nseg, uint64_t* d_hash, void* stream)
+{
+    TraceArgs a;
+    int st = prepare(t, d_src, n_src, nside, 1, mode, a, "rt_trace_paths");
+    if (st != RT_OK) return st;
+    if (n_src == 0) return RT_OK;
+    a.nseg = d_nseg;
+    a.hash = d_hash;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int fit = occupancy_fwd(1, mode, 1, a.t.uniform_level >= 0, g_block);
+    if (cudaMemsetAsync(&t->st->queue, 0, sizeof(unsigned long long), s) != cudaSuccess)
+        return cuda_error("rt_trace_paths: queue reset");
+    if (launch_paths(a, mode, g_block, grid_for(fit), s) != cudaSuccess)
+        return cuda_error("rt_trace_paths: launch");
+    return RT_OK;
+}
+
+int rt_trace_columns_adjoint(const rt_octree* t, const double* d_src, int64_t n_src, int nside,
+                             const void* d_grad_out, int n_species, int mode, double* d_grad_dens,
+                             int path_policy, void* stream)
+{
+    TraceArgs a;
+    int st = prepare(t, d_src, n_src, nside, n_species, mode, a, "rt_trace_columns_adjoint");
+    if (st != RT_OK) return st;
+    if (path_policy != 0 && path_policy != 1)
+        return set_error(RT_ERR_ARG, "rt_trace_columns_adjoint: only path_policy 0 (auto) and 1 (recompute) exist");
+    if (n_src == 0) return RT_OK;
+    if (!d_grad_out || !d_grad_dens) return set_error(RT_ERR_ARG, "rt_trace_columns_adjoint: null gradient pointer");
+    if (!aligned16(d_grad_out) || !aligned16(d_grad_dens))
+        return set_error(RT_ERR_ARG, "rt_trace_columns_adjoint: gradients must be 16-byte aligned");
+    a.gin = d_grad_out;
+    a.out = d_grad_dens;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int fit = occupancy_adj(mode, n_species, a.t.uniform_level >= 0, g_block);
+    if (cudaMemsetAsync(&t->st->queue, 0, sizeof(unsigned long long), s) != cudaSuccess)
+        return cuda_error("rt_trace_columns_adjoint: queue reset");
+    if (launch_adjoint(a, mode, g_block, grid_for(fit), s) != cudaSuccess)
+        return cuda_error("rt_trace_columns_adjoint: launch");
+    return RT_OK;
+}
+
+int rt_get_stats(const rt_octree* t, rt_stats* h_out, void* stream)
+{
+    if (!t || !h_out) return set_error(RT_ERR_ARG, "rt_get_stats: null argument");
+    DevStats d;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (cudaMemcpyAsync(&d, t->st, sizeof d, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return cuda_error("rt_get_stats");
+    h_out->rays = d.rays;
+    h_out->segments = d.segments;
+    h_out->exit_fallbacks = d.exit_fb;
+    h_out->lookup_fallbacks = d.lookup_fb;
+    h_out->status = d.status;
+    h_out->reserved = 0;
+    h_out->fault_ray = d.status ? d.fault_ray : -1;
+    return RT_OK;
+}
+
+int rt_reset_stats(rt_octree* t, void* stream)
+{
+    if (!t) return set_error(RT_ERR_ARG, "rt_reset_stats: null octree");
+    if (cudaMemsetAsync(t->st, 0, sizeof(DevStats), (cudaStream_t)stream) != cudaSuccess)
+        return cuda_error("rt_reset_stats");
+    return RT_OK;
+}
+
+}  // extern "C"

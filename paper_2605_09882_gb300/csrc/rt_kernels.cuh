@@ -1,0 +1,188 @@
+// Persistent trace kernels: a warp pops 32 * kRayBatch consecutive rays from
+// a global counter (one atomic per pop, no waiting), each lane walks one ray.
+// Ray r of the padded space maps direction-major: q = r / n_src_pad,
+// s = r % n_src_pad, so a warp walks 32 neighbouring sources (Morton order)
+// along one direction and the warps resident at any time sweep one compact
+// region of the cloud, which keeps the leaves they gather in L2.
+#pragma once
+
+#include "rt_device.cuh"
+
+namespace rt {
+
+constexpr int kRayBatch = 4;  // 32-ray groups per queue pop
+
+// ----------------------------------------------------------------- visitors
+
+template <int SM>
+struct FwdKahan {  // FP32 columns with Kahan compensation
+    float sum[SM], cmp[SM];
+    const void* dens;
+    int f64, S;
+    __device__ __forceinline__ void init()
+    {
+#pragma unroll
+        for (int k = 0; k < SM; k++) sum[k] = cmp[k] = 0.f;
+    }
+    template <class F>
+    __device__ __forceinline__ void seg(uint32_t j, F dsin)
+    {
+        const float ds = (float)dsin;
+        float n[SM];
+        load_dens<SM, float>(dens, f64, S, j, n);
+#pragma unroll
+        for (int k = 0; k < SM; k++) {
+            const float y = __fmaf_rn(n[k], ds, -cmp[k]);
+            const float tt = __fadd_rn(sum[k], y);
+            cmp[k] = __fsub_rn(__fsub_rn(tt, sum[k]), y);
+            sum[k] = tt;
+        }
+    }
+};
+
+template <int SM>
+struct FwdF64 {  // FP64 columns, plain summation in path order
+    double col[SM];
+    const void* dens;
+    int f64, S;
+    __device__ __forceinline__ void init()
+    {
+#pragma unroll
+        for (int k = 0; k < SM; k++) col[k] = 0.0;
+    }
+    template <class F>
+    __device__ __forceinline__ void seg(uint32_t j, F dsin)
+    {
+        const double ds = (double)dsin;
+        double n[SM];
+        load_dens<SM, double>(dens, f64, S, j, n);
+#pragma unroll
+        for (int k = 0; k < SM; k++) col[k] = __dadd_rn(col[k], __dmul_rn(n[k], ds));
+    }
+};
+
+struct PathHash {
+    uint64_t h;
+    __device__ __forceinline__ void init() { h = 0xcbf29ce484222325ull; }
+    template <class F>
+    __device__ __forceinline__ void seg(uint32_t j, F) { h = (h ^ (uint64_t)j) * 0x100000001b3ull; }
+};
+
+template <int SM>
+struct AdjScatter {  // grad[j,k] += g[k] * ds
+    double g[SM];
+    double* grad;
+    int S;
+    template <class F>
+    __device__ __forceinline__ void seg(uint32_t j, F dsin)
+    {
+        const double ds = (double)dsin;
+        double* p = grad + (size_t)j * S;
+#pragma unroll
+        for (int k = 0; k < SM; k++)
+            if (k < S) atomicAdd(p + k, __dmul_rn(g[k], ds));
+    }
+};
+
+// ------------------------------------------------------------ common loop
+
+__device__ __forceinline__ void flush_counters(DevStats* st, unsigned long long rays,
+                                               unsigned long long segs, unsigned long long efb,
+                                               unsigned long long lfb)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        rays += __shfl_down_sync(RT_FULL, rays, o);
+        segs += __shfl_down_sync(RT_FULL, segs, o);
+        efb += __shfl_down_sync(RT_FULL, efb, o);
+        lfb += __shfl_down_sync(RT_FULL, lfb, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (rays) atomicAdd(&st->rays, rays);
+        if (segs) atomicAdd(&st->segments, segs);
+        if (efb) atomicAdd(&st->exit_fb, efb);
+        if (lfb) atomicAdd(&st->lookup_fb, lfb);
+    }
+}
+
+// KIND 0: forward columns; 1: path fingerprints; 2: adjoint scatter.
+template <int KIND, int MODE, bool UNIFORM, int SM>
+__global__ void __launch_bounds__(256) k_trace(const TraceArgs a)
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned long long total = (unsigned long long)a.n_src_pad * (unsigned long long)a.nd;
+    const long long cap = a.t.step_cap;
+    unsigned long long n_rays = 0, n_segs = 0, n_efb = 0, n_lfb = 0;
+    for (;;) {
+        unsigned long long base = 0;
+        if (lane == 0) base = atomicAdd(&a.st->queue, 32ull * kRayBatch);
+        base = __shfl_sync(RT_FULL, base, 0);
+        if (base >= total) break;
+        for (int kk = 0; kk < kRayBatch; kk++) {
+            const unsigned long long g0 = base + 32ull * kk;
+            if (g0 >= total) break;
+            const int q = (int)(g0 / (unsigned long long)a.n_src_pad);
+            const long long s = (long long)(g0 - (unsigned long long)q * a.n_src_pad) + lane;
+            if (s >= a.n_src) continue;
+            const DirConst d = a.dirs[q];
+            const long long ray = s * a.nd + q;
+            const double* src = a.src + 3 * s;
+            WalkCounters wc = {0u, 0u, 0u};
+            if (KIND == 0) {
+                if (MODE == RT_MODE_FP64) {
+                    FwdF64<SM> v;
+                    v.dens = a.dens; v.f64 = a.dens_f64; v.S = a.S;
+                    v.init();
+                    const int st = walk<MODE, UNIFORM>(a.t, d, src, cap, v, wc);
+                    if (st != RT_OK) { report_fault(a.st, st, ray); v.init(); }
+                    double* o = (double*)a.out + (size_t)ray * a.S;
+#pragma unroll
+                    for (int k = 0; k < SM; k++)
+                        if (k < a.S) o[k] = v.col[k];
+                } else {
+                    FwdKahan<SM> v;
+                    v.dens = a.dens; v.f64 = a.dens_f64; v.S = a.S;
+                    v.init();
+                    const int st = walk<MODE, UNIFORM>(a.t, d, src, cap, v, wc);
+                    if (st != RT_OK) { report_fault(a.st, st, ray); v.init(); }
+                    float* o = (float*)a.out + (size_t)ray * a.S;
+                    if (SM == 4 && a.S == 4) {
+                        *(float4*)o = make_float4(v.sum[0], v.sum[1], v.sum[2], v.sum[3]);
+                    } else {
+#pragma unroll
+                        for (int k = 0; k < SM; k++)
+                            if (k < a.S) o[k] = v.sum[k];
+                    }
+                }
+            } else if (KIND == 1) {
+                PathHash v;
+                v.init();
+                const int st = walk<MODE, UNIFORM>(a.t, d, src, cap, v, wc);
+                if (st != RT_OK) { report_fault(a.st, st, ray); v.h = 0; wc.nseg = 0; }
+                if (a.nseg) a.nseg[ray] = wc.nseg;
+                if (a.hash) a.hash[ray] = v.h;
+            } else {
+                AdjScatter<SM> v;
+                v.grad = (double*)a.out;
+                v.S = a.S;
+#pragma unroll
+                for (int k = 0; k < SM; k++) {
+                    v.g[k] = 0.0;
+                    if (k < a.S)
+                        v.g[k] = (MODE == RT_MODE_FP64)
+                                     ? __ldg((const double*)a.gin + (size_t)ray * a.S + k)
+                                     : (double)__ldg((const float*)a.gin + (size_t)ray * a.S + k);
+                }
+                const int st = walk<MODE, UNIFORM>(a.t, d, src, cap, v, wc);
+                if (st != RT_OK) report_fault(a.st, st, ray);
+            }
+            n_rays++;
+            n_segs += wc.nseg;
+            n_efb += wc.exit_fb;
+            n_lfb += wc.lookup_fb;
+        }
+    }
+    flush_counters(a.st, n_rays, n_segs, n_efb, n_lfb);
+}
+
+}  // namespace rt
