@@ -1,0 +1,82 @@
+"""Full-size parity at 512^3, Nside 1 (the benchmark workload, in the launch
+configuration the benchmark times): the whole trace runs on the GPU; the
+oracle recomputes a random sample of sources one by one.
+
+Bars: path fingerprints (segment count, hash) of the sampled rays equal the
+oracle's; F32-Kahan columns within 1e-5 relative (+1e-30); FP64-form columns
+bitwise equal to the oracle's.  Max and mean error per species are printed.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+N_SAMPLE = 3000
+
+
+@pytest.fixture(scope="module")
+def setup():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2605_09882_gb300 as rt
+    from synth import torchgen
+    keys, lev, dens, _ = torchgen.uniform_cloud(9, 2.0, 5, device="cuda")
+    n = keys.numel()
+    src = torchgen.uniform_centres(9, torch.arange(n, device="cuda"))
+    tree = rt.Octree(keys, lev)
+    rng = np.random.default_rng(55)
+    idx = np.sort(rng.choice(n, size=N_SAMPLE, replace=False))
+    # edge sources too: the first and last leaves and the box corners
+    idx = np.unique(np.concatenate([idx, [0, 1, n - 1, n - 2, (n - 1) // 7]]))
+    keys_h = keys.cpu().numpy().view(np.uint64)
+    lev_h = lev.cpu().numpy()
+    dens_h = dens.cpu().numpy().astype(np.float64)
+    src_h = synth.leaf_centres(synth.Cloud(keys_h[idx], lev_h[idx], np.zeros((len(idx), 1)), (1 << 21,) * 3))
+    assert np.array_equal(src_h, src[torch.from_numpy(idx).cuda()].cpu().numpy())
+    want, h_or, n_or = oracle.trace(keys_h, lev_h, dens_h, src_h, oracle.healpix(1))
+    yield dict(rt=rt, torch=torch, tree=tree, src=src, dens=dens, idx=idx, want=want, h_or=h_or,
+               n_or=n_or, n=n)
+    tree.close()
+
+
+def test_f32k_full_trace_sampled(setup):
+    rt, torch = setup["rt"], setup["torch"]
+    tree = setup["tree"]
+    tree.reset_stats()
+    out = rt.trace_columns(tree, setup["src"], 1, setup["dens"], "f32k")
+    st = tree.stats()
+    assert st["status"] == 0, st
+    got = out[torch.from_numpy(setup["idx"]).cuda()].double().cpu().numpy()
+    want = setup["want"]
+    d = np.abs(got - want)
+    assert np.all(d <= 1e-5 * np.abs(want) + 1e-30)
+    rel = d / np.abs(want)
+    print("f32k rel err max per species", rel.max(axis=(0, 1)), "mean", rel.mean(axis=(0, 1)))
+    print("segments", st["segments"], "exit fallbacks", st["exit_fallbacks"])
+    del out
+
+
+def test_paths_full_trace_sampled(setup):
+    rt, torch = setup["rt"], setup["torch"]
+    nseg, hsh = rt.trace_paths(setup["tree"], setup["src"], 1, "f32k")
+    sel = torch.from_numpy(setup["idx"]).cuda()
+    np.testing.assert_array_equal(nseg[sel].cpu().numpy().astype(np.uint64), setup["n_or"])
+    np.testing.assert_array_equal(hsh[sel].cpu().numpy().view(np.uint64), setup["h_or"])
+    # segments per ray in the whole trace (the benchmark's unit count)
+    total = int(nseg.sum(dtype=torch.int64))
+    print("total segments", total, "per ray", total / nseg.numel())
+    assert total > 5e11
+
+
+def test_fp64_full_trace_sampled(setup):
+    rt, torch = setup["rt"], setup["torch"]
+    tree = setup["tree"]
+    tree.reset_stats()
+    out = rt.trace_columns(tree, setup["src"], 1, setup["dens"], "fp64")
+    assert tree.stats()["status"] == 0
+    got = out[torch.from_numpy(setup["idx"]).cuda()].cpu().numpy()
+    np.testing.assert_array_equal(got, setup["want"])
