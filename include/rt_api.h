@@ -157,9 +157,10 @@ int rt_reset_stats(rt_octree* tree, void* stream);
 int rt_set_step_cap(rt_octree* tree, int64_t cap);
 
 /* Launch shape of the persistent trace kernels: threads per block (a
- * multiple of 32, 32..1024; 0 = default 256) and resident blocks per SM (0 =
- * as many as fit).  Applies to later calls in this process. */
-int rt_set_launch(int threads_per_block, int blocks_per_sm);
+ * multiple of 32 in 32..256; 0 = default 256), resident blocks per SM (0 =
+ * as many as fit) and 32-ray groups a warp takes per work-queue pop (1..64;
+ * 0 = default 4).  Applies to later calls in this process. */
+int rt_set_launch(int threads_per_block, int blocks_per_sm, int groups_per_pop);
 
 /* Lookup choice: 1 (default) lets a full cube of equal-level leaves use the
  * O(1) Morton index; 0 forces the coarse table and key search even then

@@ -57,7 +57,7 @@ def _load():
     lib.rt_get_stats.argtypes = [P, C.POINTER(Stats), P]
     lib.rt_reset_stats.argtypes = [P, P]
     lib.rt_set_step_cap.argtypes = [P, i64]
-    lib.rt_set_launch.argtypes = [i32, i32]
+    lib.rt_set_launch.argtypes = [i32, i32, i32]
     lib.rt_set_lookup.argtypes = [P, i32]
     lib.rt_octree_info.argtypes = [P, C.POINTER(i64), C.POINTER(i32), C.POINTER(i32)]
     lib.rt_last_error.restype = C.c_char_p
@@ -90,8 +90,9 @@ def healpix_dirs(nside: int) -> np.ndarray:
     return out
 
 
-def set_launch(threads_per_block: int = 0, blocks_per_sm: int = 0):
-    _check(_lib.rt_set_launch(int(threads_per_block), int(blocks_per_sm)))
+def set_launch(threads_per_block: int = 0, blocks_per_sm: int = 0, groups_per_pop: int = 0):
+    """Launch shape of the persistent kernels (0 = default for each)."""
+    _check(_lib.rt_set_launch(int(threads_per_block), int(blocks_per_sm), int(groups_per_pop)))
 
 
 class Octree:

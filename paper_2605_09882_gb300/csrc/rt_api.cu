@@ -32,6 +32,7 @@ void clear_error() { g_err.clear(); }
 
 static int g_block = 256;
 static int g_blocks_per_sm = 0;
+static int g_batch = 4;
 
 struct DeviceInfo {
     int sms = 0;
@@ -150,6 +151,7 @@ static int prepare(const rt_octree* t, const double* d_src, int64_t n_src, int n
     a.n_src_pad = (n_src + 31) / 32 * 32;
     a.S = S;
     a.st = t->st;
+    a.batch = g_batch;
     return RT_OK;
 }
 
@@ -179,14 +181,18 @@ void rt_destroy_octree(rt_octree* t)
     free(t);
 }
 
-int rt_set_launch(int threads_per_block, int blocks_per_sm)
+int rt_set_launch(int threads_per_block, int blocks_per_sm, int groups_per_pop)
 {
     if (threads_per_block == 0) threads_per_block = 256;
+    if (groups_per_pop == 0) groups_per_pop = 4;
     if (threads_per_block < 32 || threads_per_block > 256 || threads_per_block % 32)
         return set_error(RT_ERR_ARG, "rt_set_launch: threads_per_block must be a multiple of 32 in [32, 256]");
     if (blocks_per_sm < 0) return set_error(RT_ERR_ARG, "rt_set_launch: blocks_per_sm < 0");
+    if (groups_per_pop < 1 || groups_per_pop > 64)
+        return set_error(RT_ERR_ARG, "rt_set_launch: groups_per_pop must be in [1, 64]");
     g_block = threads_per_block;
     g_blocks_per_sm = blocks_per_sm;
+    g_batch = groups_per_pop;
     return RT_OK;
 }
 

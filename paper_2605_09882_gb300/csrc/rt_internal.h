@@ -65,6 +65,7 @@ struct TraceArgs {
     uint32_t* nseg;          // path fingerprints (optional)
     uint64_t* hash;
     DevStats* st;
+    int batch;               // 32-ray groups per queue pop
 };
 
 // Launch helpers (defined in the .cu files).

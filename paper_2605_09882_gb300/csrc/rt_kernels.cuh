@@ -1,4 +1,4 @@
-// Persistent trace kernels: a warp pops 32 * kRayBatch consecutive rays from
+// Persistent trace kernels: a warp pops 32 * batch consecutive rays from
 // a global counter (one atomic per pop, no waiting), each lane walks one ray.
 // Ray r of the padded space maps direction-major: q = r / n_src_pad,
 // s = r % n_src_pad, so a warp walks 32 neighbouring sources (Morton order)
@@ -10,7 +10,6 @@
 
 namespace rt {
 
-constexpr int kRayBatch = 4;  // 32-ray groups per queue pop
 
 // ----------------------------------------------------------------- visitors
 
@@ -115,10 +114,10 @@ __global__ void __launch_bounds__(256) k_trace(const TraceArgs a)
     unsigned long long n_rays = 0, n_segs = 0, n_efb = 0, n_lfb = 0;
     for (;;) {
         unsigned long long base = 0;
-        if (lane == 0) base = atomicAdd(&a.st->queue, 32ull * kRayBatch);
+        if (lane == 0) base = atomicAdd(&a.st->queue, 32ull * (unsigned)a.batch);
         base = __shfl_sync(RT_FULL, base, 0);
         if (base >= total) break;
-        for (int kk = 0; kk < kRayBatch; kk++) {
+        for (int kk = 0; kk < a.batch; kk++) {
             const unsigned long long g0 = base + 32ull * kk;
             if (g0 >= total) break;
             const int q = (int)(g0 / (unsigned long long)a.n_src_pad);

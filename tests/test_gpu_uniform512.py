@@ -69,7 +69,8 @@ def test_paths_full_trace_sampled(setup):
     # segments per ray in the whole trace (the benchmark's unit count)
     total = int(nseg.sum(dtype=torch.int64))
     print("total segments", total, "per ray", total / nseg.numel())
-    assert total > 5e11
+    # every ray crosses at least one leaf; exact x/y edge ties count once
+    assert int(nseg.min()) >= 1 and total > 4e11
 
 
 def test_fp64_full_trace_sampled(setup):
