@@ -170,6 +170,52 @@ int rt_set_lookup(rt_octree* tree, int use_uniform_index);
 /* Number of leaves and the deepest level of a handle (host values). */
 int rt_octree_info(const rt_octree* tree, int64_t* n_leaves, int* max_level, int* uniform_level);
 
+/* ---------------------------------------------------------------- batches
+ * Many independent clouds (octrees of uneven size and depth) traced in one
+ * persistent launch over a single work queue, replayed as a CUDA graph
+ * (a memset node that resets the queue, then the kernel node).  An addition
+ * of this library; the paper traces one cloud with MPI/OpenMP (Alg. 1). */
+typedef struct rt_cloud_desc {
+    const rt_octree* tree;   /* built with rt_build_octree on this device */
+    const double* d_src;     /* float64 [n_src][3] */
+    int64_t n_src;
+    int nside;               /* power of two, 1..1024 */
+    int n_species;           /* 1..8 */
+    const void* d_dens;      /* [n_leaves][n_species], dens_dtype, 16-byte aligned */
+    int dens_dtype;
+    int reserved;
+    void* d_out;             /* [n_src][12 nside^2][n_species], f32 (F32-Kahan) or f64 (FP64) */
+} rt_cloud_desc;
+
+typedef struct rt_batch rt_batch; /* opaque */
+
+/* Uploads the descriptors of n_clouds clouds (copied; the pointers inside
+ * must stay valid while the batch is used) and allocates the batch's queue
+ * and statistics.  Synchronous. */
+int rt_batch_create(const rt_cloud_desc* h_desc, int n_clouds, int mode, rt_batch** out);
+
+/* Traces every ray of every cloud in one launch, enqueued on `stream` as a
+ * CUDA graph; the graph is built on the first call and rebuilt only when the
+ * launch shape (rt_set_launch) changes.  Outputs as rt_trace_columns. */
+int rt_batch_launch(rt_batch* batch, void* stream);
+
+/* Statistics of the batch (synchronizes `stream`) / zeroes them (enqueued). */
+int rt_batch_stats(const rt_batch* batch, rt_stats* h_out, void* stream);
+int rt_batch_reset_stats(rt_batch* batch, void* stream);
+
+/* Frees the batch (synchronizes the device first).  NULL is ignored. */
+void rt_batch_destroy(rt_batch* batch);
+
+/* Picks the launch shape of `batch` by timing: threads per block in
+ * {64, 128, 256} x resident blocks per SM, then 32-ray groups per queue pop,
+ * each measured with CUDA events over two launches on `stream`.  The best is
+ * applied with rt_set_launch and, if cache_json is not NULL, stored there
+ * keyed by (GPU name, SM count, mode, clouds, rays, max species); a later
+ * call with a matching key applies the cached shape without timing.
+ * h_best (optional): int[3] = {threads, blocks per SM, groups per pop};
+ * h_rate (optional): segments/s of the best shape. */
+int rt_autotune(rt_batch* batch, const char* cache_json, int* h_best, double* h_rate, void* stream);
+
 /* Message of the last failed call on this host thread ("" if none). */
 const char* rt_last_error(void);
 

@@ -14,7 +14,7 @@ import numpy as np
 
 from . import _build
 
-__all__ = ["Octree", "healpix_dirs", "trace_columns", "trace_paths", "trace_columns_adjoint",
+__all__ = ["Octree", "Batch", "healpix_dirs", "trace_columns", "trace_paths", "trace_columns_adjoint",
            "Columns", "RTError", "MODE_FP64", "MODE_F32_KAHAN", "set_launch", "lib_path"]
 
 MODE_FP64, MODE_F32_KAHAN = 0, 1
@@ -28,6 +28,12 @@ class RTError(RuntimeError):
     def __init__(self, code: int, msg: str):
         super().__init__(f"{STATUS.get(code, code)}: {msg}")
         self.code = code
+
+
+class CloudDesc(C.Structure):
+    _fields_ = [("tree", C.c_void_p), ("d_src", C.c_void_p), ("n_src", C.c_int64), ("nside", C.c_int),
+                ("n_species", C.c_int), ("d_dens", C.c_void_p), ("dens_dtype", C.c_int),
+                ("reserved", C.c_int), ("d_out", C.c_void_p)]
 
 
 class Stats(C.Structure):
@@ -61,6 +67,13 @@ def _load():
     lib.rt_set_lookup.argtypes = [P, i32]
     lib.rt_octree_info.argtypes = [P, C.POINTER(i64), C.POINTER(i32), C.POINTER(i32)]
     lib.rt_last_error.restype = C.c_char_p
+    lib.rt_batch_create.argtypes = [P, i32, i32, C.POINTER(P)]
+    lib.rt_batch_launch.argtypes = [P, P]
+    lib.rt_batch_stats.argtypes = [P, C.POINTER(Stats), P]
+    lib.rt_batch_reset_stats.argtypes = [P, P]
+    lib.rt_batch_destroy.argtypes = [P]
+    lib.rt_batch_destroy.restype = None
+    lib.rt_autotune.argtypes = [P, C.c_char_p, C.POINTER(C.c_int * 3), C.POINTER(C.c_double), P]
     return lib
 
 
@@ -214,6 +227,65 @@ def trace_columns_adjoint(tree: Octree, src, nside: int, grad_out, mode="f32k", 
     _check(_lib.rt_trace_columns_adjoint(tree.handle, _dptr(src), int(src.shape[0]), int(nside),
                                          _dptr(grad_out), S, m, _dptr(grad_dens), 1, _stream(stream)))
     return grad_dens
+
+
+class Batch:
+    """Many clouds traced in one persistent launch, replayed as a CUDA graph.
+    clouds: sequence of (tree, src, nside, dens); outputs are allocated here
+    (float32 for F32-Kahan, float64 for FP64) and returned by .outputs."""
+
+    def __init__(self, clouds, mode="f32k"):
+        import torch
+        self.mode = _mode(mode)
+        odt = torch.float32 if self.mode == MODE_F32_KAHAN else torch.float64
+        self._keep, self.outputs = [], []
+        descs = (CloudDesc * len(clouds))()
+        for i, (tree, src, nside, dens) in enumerate(clouds):
+            src = _check_src(src)
+            dens = dens.contiguous()
+            if dens.dim() == 1:
+                dens = dens[:, None]
+            out = torch.empty((src.shape[0], 12 * nside * nside, dens.shape[1]), dtype=odt, device=src.device)
+            self._keep += [tree, src, dens]
+            self.outputs.append(out)
+            descs[i] = CloudDesc(tree.handle.value, src.data_ptr(), src.shape[0], nside, dens.shape[1],
+                                 dens.data_ptr(), F64 if dens.dtype == torch.float64 else F32, 0,
+                                 out.data_ptr())
+        h = C.c_void_p()
+        _check(_lib.rt_batch_create(descs, len(clouds), self.mode, C.byref(h)))
+        self._h = h
+
+    def launch(self, stream=None):
+        _check(_lib.rt_batch_launch(self._h, _stream(stream)))
+        return self.outputs
+
+    def stats(self, stream=None) -> dict:
+        s = Stats()
+        _check(_lib.rt_batch_stats(self._h, C.byref(s), _stream(stream)))
+        return {f: getattr(s, f) for f, _ in Stats._fields_ if f != "reserved"}
+
+    def reset_stats(self, stream=None):
+        _check(_lib.rt_batch_reset_stats(self._h, _stream(stream)))
+
+    def autotune(self, cache_json=None, stream=None):
+        """Times launch shapes and applies the best; returns ((threads,
+        blocks_per_sm, groups_per_pop), segments/s)."""
+        best = (C.c_int * 3)()
+        rate = C.c_double()
+        _check(_lib.rt_autotune(self._h, cache_json.encode() if cache_json else None, C.byref(best),
+                                C.byref(rate), _stream(stream)))
+        return tuple(best), rate.value
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.rt_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 try:

@@ -15,7 +15,7 @@ LIB = os.path.join(OUT_DIR, "libraytheia_gb300.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC",
               "-Xcompiler", "-ffp-contract=off", "-Xcompiler", "-fno-strict-aliasing"]
-CUDA_SOURCES = ["rt_api.cu", "rt_octree.cu", "rt_forward.cu", "rt_adjoint.cu"]
+CUDA_SOURCES = ["rt_api.cu", "rt_octree.cu", "rt_forward.cu", "rt_adjoint.cu", "rt_batched.cu"]
 CXX_SOURCES = ["rt_healpix.cpp"]
 
 
@@ -37,7 +37,7 @@ def build(verbose: bool = False, ptxas_info: bool = False) -> str:
     jobs = []
     for src in CUDA_SOURCES:
         obj = os.path.join(obj_dir, src + ".o")
-        flags = NVCC_FLAGS + (["-Xptxas", "-v"] if ptxas_info else [])
+        flags = NVCC_FLAGS + (["-Xptxas", "-v"] if ptxas_info else []) + os.environ.get("RT_NVCC_FLAGS", "").split()
         jobs.append([nvcc(), *ARCH, *flags, "-c", os.path.join(CSRC, src), "-o", obj])
     for src in CXX_SOURCES:
         obj = os.path.join(obj_dir, src + ".o")

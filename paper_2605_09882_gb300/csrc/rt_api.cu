@@ -112,6 +112,17 @@ static const DirConst* dir_table(int dev, int nside, int* status)
     return dptr;
 }
 
+void launch_shape(int* block, int* blocks_per_sm, int* groups_per_pop)
+{
+    *block = g_block;
+    *blocks_per_sm = g_blocks_per_sm;
+    *groups_per_pop = g_batch;
+}
+
+const DirConst* direction_table(int dev, int nside, int* status) { return dir_table(dev, nside, status); }
+
+int sm_count_of(int dev) { return sm_count(dev); }
+
 static bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 
 // Common argument handling of the trace entry points.

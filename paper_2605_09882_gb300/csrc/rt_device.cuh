@@ -482,12 +482,180 @@ __device__ __forceinline__ int walk_f32k(const DevTree& t, const DirConst& d,
     return RT_OK;
 }
 
+// ------------------------------------ F32-Kahan walk on a uniform grid
+
+// Double-float exit time t = (A - ph - pl) * (ih + il) (depth-21 units) of one
+// axis: th = fl(fl(A - ph) * ih) is the FP32 time the certified bound is stated
+// for, th + tl carries about 44 bits.
+__device__ __forceinline__ void exit_time(float Af, float ph, float pl, float ih, float il, float& th,
+                                          float& tl)
+{
+    const float s = __fsub_rn(Af, ph);
+    const float bb = __fsub_rn(s, Af);
+    const float e1 = __fadd_rn(__fsub_rn(Af, __fsub_rn(s, bb)), __fsub_rn(-ph, bb));
+    const float rl = __fsub_rn(e1, pl);
+    th = __fmul_rn(s, ih);
+    tl = __fadd_rn(__fmaf_rn(s, ih, -th), __fmaf_rn(s, il, __fmul_rn(rl, ih)));
+}
+
+// Exit set when the two smallest FP32 times are within the certified margin:
+// axes that tie exactly (bitwise-equal |inv| and equal |D|) are recognised in
+// integers, anything else is decided by the FP64 times of the definition.
+template <int VM>
+__device__ __forceinline__ unsigned resolve_exit(const float th[3], const float Af[3], const uint32_t qf[3],
+                                                 const float ih[3], int flags,
+                                                 const DirConst* __restrict__ dp, int bs, WalkCounters& wc)
+{
+    unsigned E = 1u << bs;
+    bool amb = false;
+    const float tmin = sel3(th, bs);
+    const long long Ds = ((long long)__float2int_rn(sel3(Af, bs)) << 32) - (long long)sel3(qf, bs);
+    const float errs = fabsf(tmin) * kER + fabsf(sel3(ih, bs)) * kEA;
+#pragma unroll
+    for (int b = 0; b < 3; b++) {
+        if ((VM & (1 << b)) && b != bs) {
+            const float errb = fabsf(th[b]) * kER + fabsf(ih[b]) * kEA;
+            if (__fsub_rn(th[b], tmin) <= errs + errb) {
+                const long long Db = ((long long)__float2int_rn(Af[b]) << 32) - (long long)qf[b];
+                if (inv_equal(flags, b, bs) && llabs(Db) == llabs(Ds)) E |= 1u << b;
+                else amb = true;
+            }
+        }
+    }
+    if (amb) {
+        wc.exit_fb++;
+        double tb[3];
+        double mn = __longlong_as_double(0x7ff0000000000000ll);
+#pragma unroll
+        for (int b = 0; b < 3; b++) {
+            tb[b] = mn;
+            if (VM & (1 << b)) {
+                const long long D = ((long long)__float2int_rn(Af[b]) << 32) - (long long)qf[b];
+                tb[b] = __dmul_rn(__dmul_rn(__ll2double_rn(D), 0x1p-53), __ldg(&dp->inv[b]));
+            }
+        }
+#pragma unroll
+        for (int b = 0; b < 3; b++) mn = fmin(mn, tb[b]);
+        E = 0;
+#pragma unroll
+        for (int b = 0; b < 3; b++)
+            if ((VM & (1 << b)) && tb[b] == mn) E |= 1u << b;
+    }
+    return E;
+}
+
+// Walk of one ray through a full cube of equal-level leaves (level L <= 10),
+// F32-Kahan arithmetic, for a direction whose moving axes are the bits of VM.
+// The leaf index is the level-L Morton index, kept per axis in dilated form;
+// the per-axis far-face distance A (exact integer and exact float) and the
+// double-float exit time change only on the axes that step.
+template <int VM, class V>
+__device__ __forceinline__ int walk_f32k_grid(const DevTree& t, const DirConst* __restrict__ dp,
+                                              const double* __restrict__ src, long long cap, V& vis,
+                                              WalkCounters& wc)
+{
+    constexpr int nvm = ((VM >> 0) & 1) + ((VM >> 1) & 1) + ((VM >> 2) & 1);
+    const int sh = kDepth - t.uniform_level;
+    const int N1 = (1 << t.uniform_level) - 1;
+    const int size = 1 << sh;
+    const int flags = __ldg(&dp->flags);
+    float ih[3], il[3];
+    uint32_t qf[3];
+    float ph[3], pl[3];
+    int c[3];
+    float Af[3], th[3], tl[3];
+    uint32_t dl[3];
+    float cE = 0.f;
+#pragma unroll
+    for (int b = 0; b < 3; b++) {
+        long long q;
+        if (!fixed_source(src[b], q)) return RT_ERR_SOURCE_OUTSIDE;
+        const int qi = (int)(q >> 32);
+        qf[b] = (uint32_t)(q & 0xffffffffll);
+        if ((uint32_t)qi >= t.ext[b]) return RT_ERR_SOURCE_OUTSIDE;
+        const float fh = __uint2float_rn(qf[b]);
+        const long long back = (long long)__float2ull_rz(fh);
+        ph[b] = fh * 0x1p-32f;
+        pl[b] = __ll2float_rn((long long)qf[b] - back) * 0x1p-32f;
+        c[b] = qi >> sh;
+        dl[b] = spread10((uint32_t)c[b]) << b;
+        Af[b] = 0.f;
+        th[b] = tl[b] = ih[b] = il[b] = 0.f;
+        if (VM & (1 << b)) {
+            ih[b] = __ldg(&dp->ih[b]);
+            il[b] = __ldg(&dp->il[b]);
+            const int pos = (flags >> (3 + b)) & 1;
+            Af[b] = __int2float_rn(((c[b] + pos) << sh) - qi);
+            exit_time(Af[b], ph[b], pl[b], ih[b], il[b], th[b], tl[b]);
+            cE = fmaxf(cE, fabsf(ih[b]) * kEA);
+        }
+    }
+    uint32_t j = dl[0] | dl[1] | dl[2];
+    float tih = 0.f, til = 0.f;
+    for (long long step = 0;; ++step) {
+        if (step >= cap) return RT_ERR_STEP_LIMIT;
+        vis.pre(j);
+        float tmin = __int_as_float(0x7f800000), t2 = tmin;
+        int bs = 0;
+#pragma unroll
+        for (int b = 0; b < 3; b++) {
+            if (VM & (1 << b)) {
+                if (th[b] < tmin) { t2 = tmin; tmin = th[b]; bs = b; }
+                else t2 = fminf(t2, th[b]);
+            }
+        }
+        unsigned E = 1u << bs;
+        if (nvm > 1 && !(__fsub_rn(t2, tmin) > (fabsf(t2) + fabsf(tmin)) * kER + 2.f * cE)) {
+            E = resolve_exit<VM>(th, Af, qf, ih, flags, dp, bs, wc);
+            bs = __ffs(E) - 1;
+        }
+        const float ths = sel3(th, bs), tls = sel3(tl, bs);
+        const float ds = __fmul_rn(__fadd_rn(__fsub_rn(ths, tih), __fsub_rn(tls, til)), 0x1p-21f);
+        tih = ths;
+        til = tls;
+        vis.acc(ds);
+        wc.nseg++;
+        bool leaving = false;
+#pragma unroll
+        for (int b = 0; b < 3; b++) {
+            if ((VM & (1 << b)) && (E & (1u << b))) {
+                const int pos = (flags >> (3 + b)) & 1;
+                if (c[b] == (pos ? N1 : 0)) leaving = true;
+                c[b] += pos ? 1 : -1;
+                Af[b] = __fadd_rn(Af[b], pos ? (float)size : -(float)size);
+                exit_time(Af[b], ph[b], pl[b], ih[b], il[b], th[b], tl[b]);
+                const uint32_t mb = kDilX << b;
+                dl[b] = pos ? (((dl[b] | ~mb) + (1u << b)) & mb) : ((dl[b] - (1u << b)) & mb);
+            }
+        }
+        if (leaving) break;
+        j = dl[0] | dl[1] | dl[2];
+    }
+    return RT_OK;
+}
+
+// Walk of one ray (direction *dp, in global memory) in either arithmetic form.
 template <int MODE, bool UNIFORM, class V>
-__device__ __forceinline__ int walk(const DevTree& t, const DirConst& d,
+__device__ __forceinline__ int walk(const DevTree& t, const DirConst* __restrict__ dp,
                                     const double* __restrict__ src, long long cap, V& vis,
                                     WalkCounters& wc)
 {
-    if (MODE == RT_MODE_FP64) return walk_fp64<UNIFORM>(t, d, src, cap, vis, wc);
+    if (MODE == RT_MODE_FP64) {
+        const DirConst d = *dp;
+        return walk_fp64<UNIFORM>(t, d, src, cap, vis, wc);
+    }
+    if (UNIFORM) {
+        switch (__ldg(&dp->flags) & 7) {
+        case 1: return walk_f32k_grid<1>(t, dp, src, cap, vis, wc);
+        case 2: return walk_f32k_grid<2>(t, dp, src, cap, vis, wc);
+        case 3: return walk_f32k_grid<3>(t, dp, src, cap, vis, wc);
+        case 4: return walk_f32k_grid<4>(t, dp, src, cap, vis, wc);
+        case 5: return walk_f32k_grid<5>(t, dp, src, cap, vis, wc);
+        case 6: return walk_f32k_grid<6>(t, dp, src, cap, vis, wc);
+        default: return walk_f32k_grid<7>(t, dp, src, cap, vis, wc);
+        }
+    }
+    const DirConst d = *dp;
     return walk_f32k<UNIFORM>(t, d, src, cap, vis, wc);
 }
 

@@ -11,4 +11,9 @@ namespace rt {
 int set_error(int code, const char* msg);
 int cuda_error(const char* where);
 void clear_error();
+// current launch shape (threads per block, blocks per SM cap, groups per pop)
+void launch_shape(int* block, int* blocks_per_sm, int* groups_per_pop);
+// device direction table of nside on device dev (uploaded on first use)
+const DirConst* direction_table(int dev, int nside, int* status);
+int sm_count_of(int dev);
 }  // namespace rt

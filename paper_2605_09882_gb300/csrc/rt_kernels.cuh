@@ -8,14 +8,21 @@
 
 #include "rt_device.cuh"
 
-namespace rt {
+#ifndef RT_MIN_BLOCKS
+#define RT_MIN_BLOCKS 1  // resident 256-thread blocks per SM the register budget is sized for
+#endif
 
+namespace rt {
 
 // ----------------------------------------------------------------- visitors
 
+// A visitor sees each segment in two halves: pre(j) as soon as the leaf is
+// known (the density gather is issued there) and acc(ds) once the segment
+// length is known; seg(j, ds) does both at once.
+
 template <int SM>
 struct FwdKahan {  // FP32 columns with Kahan compensation
-    float sum[SM], cmp[SM];
+    float sum[SM], cmp[SM], n[SM];
     const void* dens;
     int f64, S;
     __device__ __forceinline__ void init()
@@ -23,12 +30,11 @@ struct FwdKahan {  // FP32 columns with Kahan compensation
 #pragma unroll
         for (int k = 0; k < SM; k++) sum[k] = cmp[k] = 0.f;
     }
+    __device__ __forceinline__ void pre(uint32_t j) { load_dens<SM, float>(dens, f64, S, j, n); }
     template <class F>
-    __device__ __forceinline__ void seg(uint32_t j, F dsin)
+    __device__ __forceinline__ void acc(F dsin)
     {
         const float ds = (float)dsin;
-        float n[SM];
-        load_dens<SM, float>(dens, f64, S, j, n);
 #pragma unroll
         for (int k = 0; k < SM; k++) {
             const float y = __fmaf_rn(n[k], ds, -cmp[k]);
@@ -37,11 +43,13 @@ struct FwdKahan {  // FP32 columns with Kahan compensation
             sum[k] = tt;
         }
     }
+    template <class F>
+    __device__ __forceinline__ void seg(uint32_t j, F ds) { pre(j); acc(ds); }
 };
 
 template <int SM>
 struct FwdF64 {  // FP64 columns, plain summation in path order
-    double col[SM];
+    double col[SM], n[SM];
     const void* dens;
     int f64, S;
     __device__ __forceinline__ void init()
@@ -49,38 +57,46 @@ struct FwdF64 {  // FP64 columns, plain summation in path order
 #pragma unroll
         for (int k = 0; k < SM; k++) col[k] = 0.0;
     }
+    __device__ __forceinline__ void pre(uint32_t j) { load_dens<SM, double>(dens, f64, S, j, n); }
     template <class F>
-    __device__ __forceinline__ void seg(uint32_t j, F dsin)
+    __device__ __forceinline__ void acc(F dsin)
     {
         const double ds = (double)dsin;
-        double n[SM];
-        load_dens<SM, double>(dens, f64, S, j, n);
 #pragma unroll
         for (int k = 0; k < SM; k++) col[k] = __dadd_rn(col[k], __dmul_rn(n[k], ds));
     }
+    template <class F>
+    __device__ __forceinline__ void seg(uint32_t j, F ds) { pre(j); acc(ds); }
 };
 
 struct PathHash {
     uint64_t h;
     __device__ __forceinline__ void init() { h = 0xcbf29ce484222325ull; }
+    __device__ __forceinline__ void pre(uint32_t j) { h = (h ^ (uint64_t)j) * 0x100000001b3ull; }
     template <class F>
-    __device__ __forceinline__ void seg(uint32_t j, F) { h = (h ^ (uint64_t)j) * 0x100000001b3ull; }
+    __device__ __forceinline__ void acc(F) {}
+    template <class F>
+    __device__ __forceinline__ void seg(uint32_t j, F) { pre(j); }
 };
 
 template <int SM>
 struct AdjScatter {  // grad[j,k] += g[k] * ds
     double g[SM];
     double* grad;
+    uint32_t jj;
     int S;
+    __device__ __forceinline__ void pre(uint32_t j) { jj = j; }
     template <class F>
-    __device__ __forceinline__ void seg(uint32_t j, F dsin)
+    __device__ __forceinline__ void acc(F dsin)
     {
         const double ds = (double)dsin;
-        double* p = grad + (size_t)j * S;
+        double* p = grad + (size_t)jj * S;
 #pragma unroll
         for (int k = 0; k < SM; k++)
             if (k < S) atomicAdd(p + k, __dmul_rn(g[k], ds));
     }
+    template <class F>
+    __device__ __forceinline__ void seg(uint32_t j, F ds) { pre(j); acc(ds); }
 };
 
 // ------------------------------------------------------------ common loop
@@ -106,7 +122,7 @@ __device__ __forceinline__ void flush_counters(DevStats* st, unsigned long long 
 
 // KIND 0: forward columns; 1: path fingerprints; 2: adjoint scatter.
 template <int KIND, int MODE, bool UNIFORM, int SM>
-__global__ void __launch_bounds__(256) k_trace(const TraceArgs a)
+__global__ void __launch_bounds__(256, RT_MIN_BLOCKS) k_trace(const TraceArgs a)
 {
     const int lane = threadIdx.x & 31;
     const unsigned long long total = (unsigned long long)a.n_src_pad * (unsigned long long)a.nd;
@@ -123,7 +139,7 @@ __global__ void __launch_bounds__(256) k_trace(const TraceArgs a)
             const int q = (int)(g0 / (unsigned long long)a.n_src_pad);
             const long long s = (long long)(g0 - (unsigned long long)q * a.n_src_pad) + lane;
             if (s >= a.n_src) continue;
-            const DirConst d = a.dirs[q];
+            const DirConst* d = a.dirs + q;
             const long long ray = s * a.nd + q;
             const double* src = a.src + 3 * s;
             WalkCounters wc = {0u, 0u, 0u};

@@ -1,0 +1,86 @@
+"""Batched multi-cloud launch (one persistent kernel over a single queue,
+replayed as a CUDA graph) and the autotuner: every cloud's columns equal the
+oracle's (F32-Kahan within 1e-5; FP64 bitwise) and the per-cloud trace's,
+on the first launch and on graph replays; the tuned shape is cached."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def clouds():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2605_09882_gb300 as rt
+    rng = np.random.default_rng(3)
+    out = []
+    for i in range(12):
+        base = int(rng.choice((6, 8, 12, 16, 24)))
+        nref = int(rng.integers(0, 3))
+        nside = int(rng.choice((1, 2)))
+        c = synth.amr_cloud(base, nref, 80.0, 1.5, 3000 + i, fracs=synth.SPECIES_FRACTIONS[:2],
+                            dtype=np.float32, max_field=64)
+        src = synth.leaf_centres(c)
+        if src.shape[0] > 3000:
+            src = src[rng.choice(src.shape[0], 3000, replace=False)]
+        tree = rt.Octree(torch.from_numpy(c.keys.view(np.int64)).cuda(), torch.from_numpy(c.levels).cuda(),
+                         extent=c.extent)
+        out.append(dict(cloud=c, src=src, nside=nside, tree=tree,
+                        src_d=torch.from_numpy(src).cuda(), dens_d=torch.from_numpy(c.dens).cuda()))
+    # one cloud with no sources
+    out.append(dict(cloud=out[0]["cloud"], src=out[0]["src"][:0], nside=1, tree=out[0]["tree"],
+                    src_d=out[0]["src_d"][:0], dens_d=out[0]["dens_d"]))
+    return rt, out
+
+
+def _oracle(c):
+    cols, _, _ = oracle.trace(c["cloud"].keys, c["cloud"].levels, c["cloud"].dens.astype(np.float64),
+                              c["src"], oracle.healpix(c["nside"]), extent=c["cloud"].extent)
+    return cols
+
+
+@pytest.mark.parametrize("mode", ["f32k", "fp64"])
+def test_batched_matches_oracle_and_replays(clouds, mode):
+    rt, cl = clouds
+    b = rt.Batch([(c["tree"], c["src_d"], c["nside"], c["dens_d"]) for c in cl], mode)
+    wants = [_oracle(c) for c in cl]
+    for launch in range(3):
+        b.reset_stats()
+        outs = [o.cpu().numpy() for o in b.launch()]
+        st = b.stats()
+        assert st["status"] == 0, st
+        for o, w in zip(outs, wants):
+            if mode == "fp64":
+                np.testing.assert_array_equal(o, w)
+            else:
+                assert np.all(np.abs(o - w) <= 1e-5 * np.abs(w) + 1e-30)
+        assert st["rays"] == sum(w.shape[0] * w.shape[1] for w in wants)
+    single = rt.trace_columns(cl[1]["tree"], cl[1]["src_d"], cl[1]["nside"], cl[1]["dens_d"], mode)
+    np.testing.assert_array_equal(single.cpu().numpy(), outs[1])
+    b.close()
+
+
+def test_autotune_caches_best_shape(clouds, tmp_path):
+    rt, cl = clouds
+    b = rt.Batch([(c["tree"], c["src_d"], c["nside"], c["dens_d"]) for c in cl], "f32k")
+    cache = str(tmp_path / "tune.json")
+    best, rate = b.autotune(cache)
+    assert rate > 0 and best[0] in (64, 128, 256) and best[2] >= 1
+    entries = json.load(open(cache))
+    assert len(entries) == 1 and list(entries.values())[0]["threads"] == best[0]
+    best2, rate2 = b.autotune(cache)  # read back from the cache, no timing
+    assert best2 == best and abs(rate2 - rate) <= 1e-6 * rate
+    outs = [o.cpu().numpy() for o in b.launch()]
+    for o, c in zip(outs, cl):
+        w = _oracle(c)
+        assert np.all(np.abs(o - w) <= 1e-5 * np.abs(w) + 1e-30)
+    rt.set_launch(0, 0, 0)
+    b.close()
