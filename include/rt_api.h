@@ -170,6 +170,34 @@ int rt_set_lookup(rt_octree* tree, int use_uniform_index);
 /* Number of leaves and the deepest level of a handle (host values). */
 int rt_octree_info(const rt_octree* tree, int64_t* n_leaves, int* max_level, int* uniform_level);
 
+/* Forward trace that allocates no device memory (the paper has no
+ * counterpart; this is an interface addition).  It computes what
+ * rt_trace_columns computes, on a raw octree instead of a handle, for callers
+ * that cannot call cudaMalloc: an application whose own pool owns all device
+ * memory, or code that must not allocate or free because cudaMalloc and
+ * cudaFree can synchronize the whole device.
+ *   d_keys, d_levels, n_leaves, h_extent: as for rt_build_octree; the octree
+ *     is NOT validated here and must be valid (for example checked once with
+ *     rt_build_octree wherever allocation is allowed).
+ *   max_level: the deepest leaf level (sets the step cap; a full cube of
+ *     leaves all at this level uses the O(1) Morton index, any other octree a
+ *     binary search of all keys).
+ *   nside: 1, 2, 4 or 8 only; the rest as for rt_trace_columns.
+ *   h_stats: NULL, or host memory that receives this call's statistics and
+ *     status; then the call synchronizes `stream`.
+ * All scratch (work-queue counter, statistics, status word, direction table)
+ * lives in one file-scope device array of about 74 KiB that every GPU which
+ * loads the library holds until exit.  The first call on a device looks up
+ * that array's address with cudaGetSymbolAddress; make that first call
+ * before any stream capture.  Every call reuses the array and re-zeroes the
+ * counters it needs, so calls that overlap on the GPU (on different streams
+ * or threads) race and must be ordered by the caller. */
+int rt_trace_columns_noalloc(const uint64_t* d_keys, const uint8_t* d_levels, int64_t n_leaves,
+                             const int32_t* h_extent, int max_level, const double* d_src,
+                             int64_t n_src, int nside, const void* d_dens, int n_species,
+                             int dens_dtype, int mode, void* d_out, rt_stats* h_stats,
+                             void* stream);
+
 /* ---------------------------------------------------------------- batches
  * Many independent clouds (octrees of uneven size and depth) traced in one
  * persistent launch over a single work queue, replayed as a CUDA graph

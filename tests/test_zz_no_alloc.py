@@ -1,0 +1,103 @@
+"""rt_trace_columns_noalloc, the forward trace for callers that cannot allocate
+device memory (for example an application whose own pool owns all device
+memory, or code that must not call cudaMalloc/cudaFree because they can
+synchronize the device), must give what rt_trace_columns gives.
+
+It is called through the C ABI twice in a row on the same inputs, since every
+call reuses one static scratch array; each output is compared with the
+handle-based entry point's within the tolerance of the other parity tests
+(F32-Kahan: 1e-5 relative + 1e-30; FP64: bitwise).  The file is named to be
+collected last, and it builds all of its own inputs, so it also runs alone.
+"""
+import ctypes as C
+
+import numpy as np
+import pytest
+
+import synth
+from tinytrees import leaf_boxes, random_octree
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def rt():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2605_09882_gb300 as rt
+    f = rt._lib.rt_trace_columns_noalloc
+    P = C.c_void_p
+    f.argtypes = [P, P, C.c_int64, P, C.c_int, P, C.c_int64, C.c_int, P, C.c_int, C.c_int, C.c_int, P,
+                  C.POINTER(rt.Stats), P]
+    return rt
+
+
+def _dev(a):
+    import torch
+    a = np.ascontiguousarray(a)
+    if a.dtype == np.uint64:
+        a = a.view(np.int64)
+    return torch.from_numpy(a).cuda()
+
+
+def _noalloc(rt, keys, lev, max_level, src, nside, dens, mode, extent=None):
+    import torch
+    nd = 12 * nside * nside
+    S = dens.shape[1]
+    odt = torch.float32 if mode == rt.MODE_F32_KAHAN else torch.float64
+    out = torch.full((src.shape[0], nd, S), float("nan"), dtype=odt, device="cuda")
+    ext = None if extent is None else (C.c_int32 * 3)(*extent)
+    st = rt.Stats()
+    code = rt._lib.rt_trace_columns_noalloc(
+        keys.data_ptr(), lev.data_ptr(), keys.numel(), ext, max_level, src.data_ptr(), src.shape[0],
+        nside, dens.data_ptr(), S, rt.F64 if dens.dtype == torch.float64 else rt.F32, mode,
+        out.data_ptr(), C.byref(st), C.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert code == 0, rt._lib.rt_last_error()
+    assert st.status == 0 and st.rays == src.shape[0] * nd
+    return out.cpu().numpy(), st.segments
+
+
+def _compare(rt, keys_h, lev_h, dens_h, src_h, nside, extent=None):
+    keys, lev, dens, src = _dev(keys_h), _dev(lev_h), _dev(dens_h), _dev(src_h)
+    tree = rt.Octree(keys, lev, extent=extent)
+    for mode in (rt.MODE_F32_KAHAN, rt.MODE_FP64):
+        tree.reset_stats()
+        ref = rt.trace_columns(tree, src, nside, dens, mode).cpu().numpy()
+        ref_segs = tree.stats()["segments"]
+        for call in range(2):
+            got, segs = _noalloc(rt, keys, lev, int(lev_h.max()), src, nside, dens, mode, extent)
+            assert segs == ref_segs, (mode, call)
+            if mode == rt.MODE_FP64:
+                np.testing.assert_array_equal(got, ref)
+            else:
+                d = np.abs(got.astype(np.float64) - ref)
+                assert np.all(d <= 1e-5 * np.abs(ref) + 1e-30), (call, float(d.max()))
+    tree.close()
+
+
+def test_noalloc_matches_handle_entry_point_amr(rt):
+    rng = np.random.default_rng(808)
+    keys, lev, _ = random_octree(rng, 1, 7, 0.35)
+    dens = rng.uniform(0.1, 10.0, size=(keys.shape[0], 4)).astype(np.float32)
+    lo, hi = leaf_boxes(keys, lev)
+    src = np.concatenate([rng.random((300, 3)), 0.5 * (lo + hi)[::5]])
+    _compare(rt, keys, lev, dens, src, 2)
+
+
+def test_noalloc_matches_handle_entry_point_uniform(rt):
+    cloud = synth.uniform_cloud(5, 2.0, 9, fracs=synth.SPECIES_FRACTIONS, dtype=np.float32)
+    _compare(rt, cloud.keys, cloud.levels, cloud.dens, synth.leaf_centres(cloud), 1)
+
+
+def test_noalloc_rejects_oversized_direction_table(rt):
+    import torch
+    keys = _dev(np.array([0], dtype=np.uint64))
+    lev = _dev(np.array([0], dtype=np.uint8))
+    src = torch.full((1, 3), 0.5, dtype=torch.float64, device="cuda")
+    dens = torch.ones((1, 1), dtype=torch.float32, device="cuda")
+    out = torch.empty((1, 12 * 256, 1), dtype=torch.float32, device="cuda")
+    code = rt._lib.rt_trace_columns_noalloc(keys.data_ptr(), lev.data_ptr(), 1, None, 0, src.data_ptr(), 1,
+                                            16, dens.data_ptr(), 1, rt.F32, rt.MODE_F32_KAHAN,
+                                            out.data_ptr(), None, None)
+    assert code == 1 and b"nside" in rt._lib.rt_last_error()
