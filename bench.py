@@ -169,6 +169,107 @@ def cpu_model():
     return "unknown"
 
 
+# ------------------------------------------------------- other workloads
+
+def timed(fn, stream, reps=1):
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / 1e3 / reps
+
+
+def amr_leg(rt, dev, stream, check_sources=400):
+    """AMR workload: 128^3 base (sigma 1.5), field on 512^3, 2 levels above p90,
+    4 FP32 species, 1M mass-weighted sources, Nside 2, F32-Kahan; plus an
+    oracle spot check of a few hundred sources."""
+    import torch
+    from synth import torchgen
+    keys, lev, dens, ntot, ext = torchgen.amr_cloud(128, 2, 90.0, 1.5, 2, device=dev)
+    src = torchgen.mass_weighted_sources(keys, lev, ntot, 1_000_000, 102)
+    tree = rt.Octree(keys, lev, extent=ext)
+    out = torch.empty((src.shape[0], 48, 4), dtype=torch.float32, device=dev)
+    tree.reset_stats()
+    t = timed(lambda: rt.trace_columns(tree, src, 2, dens, "f32k", out=out), stream, reps=3)
+    st = tree.stats()
+    assert st["status"] == 0, st
+    segs = st["segments"] / 4
+    res = {"workload": "128^3 base AMR (2 levels above p90, %d leaves), 4 FP32 species, 1M mass-weighted "
+                       "sources, Nside 2, F32-Kahan" % keys.numel(),
+           "value": segs / t, "unit": "ray-segments/s", "ms_per_step": t * 1e3,
+           "segments_per_step": int(segs), "exit_fallbacks_per_step": st["exit_fallbacks"] / 4,
+           "lookup_fallbacks_per_step": st["lookup_fallbacks"] / 4}
+    import oracle
+    idx = torch.arange(0, src.shape[0], src.shape[0] // check_sources, device=dev)[:check_sources]
+    want, _, _ = oracle.trace(keys.cpu().numpy().view(np.uint64), lev.cpu().numpy(),
+                              dens.cpu().numpy().astype(np.float64), src[idx].cpu().numpy(),
+                              oracle.healpix(2), extent=ext)
+    got = out[idx].double().cpu().numpy()
+    err = np.abs(got - want) / np.maximum(np.abs(want), 1e-300)
+    res["parity_sample"] = {"n_src": int(idx.numel()), "max_rel": float(err.max())}
+    tree.close()
+    return res
+
+
+def batched_leg(rt, dev, stream, cache):
+    """64 independent clouds (base in {16,24,32,48,64,96}^3, 0-3 levels above
+    p80, 2 FP32 species, leaf-centre sources, Nside 1 or 2) in one launch,
+    launch shape from the autotuner."""
+    from synth import torchgen
+    g = np.random.default_rng(3)
+    clouds, keep = [], []
+    for i in range(64):
+        b = int(g.choice((16, 24, 32, 48, 64, 96)))
+        r = int(g.integers(0, 4))
+        nside = int(g.choice((1, 2)))
+        k, l, d, n, ext = torchgen.amr_cloud(b, r, 80.0, 1.5, 3000 + i, fracs=(1.0, 0.4), device=dev,
+                                             max_field=192)
+        tree = rt.Octree(k, l, extent=ext)
+        src = torchgen.leaf_centres(k, l)
+        keep.append((k, l))
+        clouds.append((tree, src, nside, d))
+    batch = rt.Batch(clouds, "f32k")
+    best, rate = batch.autotune(cache)
+    batch.reset_stats()
+    t = timed(lambda: batch.launch(), stream, reps=3)
+    st = batch.stats()
+    assert st["status"] == 0, st
+    segs = st["segments"] / 4
+    res = {"workload": "64 clouds of uneven size and depth, %d rays, one persistent launch (CUDA graph)"
+                       % (st["rays"] // 4),
+           "value": segs / t, "unit": "ray-segments/s", "ms_per_step": t * 1e3,
+           "autotuned": {"threads": best[0], "blocks_per_sm": best[1], "groups_per_pop": best[2]}}
+    batch.close()
+    rt.set_launch(0, 0, 0)
+    for c in clouds:
+        c[0].close()
+    return res
+
+
+def adjoint_leg(rt, dev, stream):
+    """Differentiable workload: 64^3 base refined once above p85, one species,
+    leaf-centre sources, Nside 2: forward (F32-Kahan) and adjoint times."""
+    import torch
+    from synth import torchgen
+    k, l, d, n, ext = torchgen.amr_cloud(64, 1, 85.0, 1.5, 4, fracs=(1.0,), device=dev)
+    tree = rt.Octree(k, l, extent=ext)
+    src = torchgen.leaf_centres(k, l)
+    out = torch.empty((src.shape[0], 48, 1), dtype=torch.float32, device=dev)
+    tf = timed(lambda: rt.trace_columns(tree, src, 2, d, "f32k", out=out), stream, reps=3)
+    g = torch.rand_like(out)
+    grad = torch.zeros((k.numel(), 1), dtype=torch.float64, device=dev)
+    ta = timed(lambda: rt.trace_columns_adjoint(tree, src, 2, g, "f32k", grad_dens=grad), stream, reps=3)
+    tree.close()
+    return {"workload": "64^3 base AMR, 1 level above p85 (%d leaves), 1 species, leaf-centre sources, Nside 2"
+                        % k.numel(), "forward_ms": tf * 1e3, "adjoint_ms": ta * 1e3,
+            "adjoint_over_forward": ta / tf}
+
+
 # -------------------------------------------------------------- reference
 
 def run_reference(a, rank, world):
@@ -319,6 +420,15 @@ def main():
         tadj = e0.elapsed_time(e1) / 1e3
         extras["adjoint"] = {"ms_per_step": tadj * 1e3, "adjoint_over_forward": tadj / avg_launch_s}
         del grad
+        torch.cuda.empty_cache()
+        # ---- octree build (validation + coarse table), one-time per tree
+        tb = timed(lambda: rt.Octree(keys, lev).close(), stream)
+        extras["build_octree_ms"] = tb * 1e3
+        # ---- the other workloads
+        extras["amr128"] = amr_leg(rt, dev, stream)
+        extras["adjoint_amr64"] = adjoint_leg(rt, dev, stream)
+        extras["batched64"] = batched_leg(rt, dev, stream,
+                                          os.path.join(ROOT, "paper_2605_09882_gb300", "autotune_gb300.json"))
         torch.cuda.empty_cache()
         # ---- CPU oracle on a sample (rank 0, N = 1) + parity of those outputs
         keys_h = keys.cpu().numpy().view(np.uint64)

@@ -272,230 +272,66 @@ __device__ __forceinline__ int walk_fp64(const DevTree& t, const DirConst& d,
 constexpr float kER = 0x1p-21f;
 constexpr float kEA = 0x1p-23f;
 
-// Walks one ray with FP32 exit tests.  Depth-21 units: a source coordinate is
-// qi + qf 2^-32 (qi integer, qf a 32-bit fraction), a face-minus-source
-// distance is D 2^-32 with D = (F - qi) 2^32 - qf an exact integer, and the
-// FP64 exit time of the definition is fl(D 2^-53 inv) box lengths.
-template <bool UNIFORM, class V>
-__device__ __forceinline__ int walk_f32k(const DevTree& t, const DirConst& d,
-                                         const double* __restrict__ src, long long cap, V& vis,
-                                         WalkCounters& wc)
-{
-    int qi[3];
-    uint32_t qf[3];
-    float ph[3], pl[3];
-    uint32_t c[3];
-#pragma unroll
-    for (int b = 0; b < 3; b++) {
-        long long q;
-        if (!fixed_source(src[b], q)) return RT_ERR_SOURCE_OUTSIDE;
-        qi[b] = (int)(q >> 32);
-        qf[b] = (uint32_t)(q & 0xffffffffll);
-        if ((uint32_t)qi[b] >= t.ext[b]) return RT_ERR_SOURCE_OUTSIDE;
-        // qf 2^-32 = ph + pl exactly (ph: 24 bits, pl: the remainder)
-        const float fh = __uint2float_rn(qf[b]);
-        const long long back = (long long)__float2ull_rz(fh);
-        ph[b] = fh * 0x1p-32f;
-        pl[b] = __ll2float_rn((long long)qf[b] - back) * 0x1p-32f;
-        c[b] = (uint32_t)qi[b];
-    }
-    uint32_t lo[3], size;
-    uint32_t ci[3], dil = 0;
-    long long j;
-    const int ush = kDepth - t.uniform_level;
-    if (UNIFORM) {
-#pragma unroll
-        for (int b = 0; b < 3; b++) ci[b] = c[b] >> ush;
-        dil = spread10(ci[0]) | (spread10(ci[1]) << 1) | (spread10(ci[2]) << 2);
-        j = dil;
-        size = 1u << ush;
-    } else {
-        uint64_t key;
-        int level;
-        j = lookup_leaf(t, c[0], c[1], c[2], key, level);
-        if (j < 0) return RT_ERR_LOOKUP_MISS;
-        leaf_box(key, level, lo, size);
-    }
-    float tih = 0.f, til = 0.f;  // t_in as a double-float (depth-21 units)
-    for (long long step = 0;; ++step) {
-        if (step >= cap) return RT_ERR_STEP_LIMIT;
-        if (UNIFORM) {
-#pragma unroll
-            for (int b = 0; b < 3; b++) lo[b] = ci[b] << ush;
-        }
-        // FP32 exit time of every moving axis
-        int A[3];
-        float tp[3];
-        int bs = 0;
-        float tmin = __int_as_float(0x7f800000);
-#pragma unroll
-        for (int b = 0; b < 3; b++) {
-            A[b] = 0;
-            tp[b] = __int_as_float(0x7f800000);
-            if (d.flags & (1 << b)) {
-                const uint32_t F = (d.flags & (8 << b)) ? lo[b] + size : lo[b];
-                A[b] = (int)F - qi[b];
-                const float x = __fsub_rn(__int2float_rn(A[b]), ph[b]);
-                tp[b] = __fmul_rn(x, d.ih[b]);
-                if (tp[b] < tmin) { tmin = tp[b]; bs = b; }
-            }
-        }
-        // certified decision; exact ties between axes of equal |inv| and equal
-        // |D| are recognised in integers, other near-ties go to FP64
-        unsigned E = 1u << bs;
-        bool amb = false;
-        {
-            const int As = sel3(A, bs);
-            const long long Ds = ((long long)As << 32) - (long long)sel3(qf, bs);
-            const float errs = fabsf(tmin) * kER + fabsf(sel3(d.ih, bs)) * kEA;
-#pragma unroll
-            for (int b = 0; b < 3; b++) {
-                if (b != bs && (d.flags & (1 << b))) {
-                    const float errb = fabsf(tp[b]) * kER + fabsf(d.ih[b]) * kEA;
-                    if (__fsub_rn(tp[b], tmin) <= errs + errb) {
-                        const long long Db = ((long long)A[b] << 32) - (long long)qf[b];
-                        if (inv_equal(d.flags, b, bs) && llabs(Db) == llabs(Ds)) E |= 1u << b;
-                        else amb = true;
-                    }
-                }
-            }
-        }
-        if (amb) {
-            wc.exit_fb++;
-            double tb[3];
-            double mn = __longlong_as_double(0x7ff0000000000000ll);
-#pragma unroll
-            for (int b = 0; b < 3; b++) {
-                tb[b] = __longlong_as_double(0x7ff0000000000000ll);
-                if (d.flags & (1 << b)) {
-                    const long long D = ((long long)A[b] << 32) - (long long)qf[b];
-                    tb[b] = __dmul_rn(__dmul_rn(__ll2double_rn(D), 0x1p-53), d.inv[b]);
-                    mn = fmin(mn, tb[b]);
-                }
-            }
-            E = 0;
-#pragma unroll
-            for (int b = 0; b < 3; b++)
-                if ((d.flags & (1 << b)) && tb[b] == mn) E |= 1u << b;
-            bs = __ffs(E) - 1;
-        }
-        // segment length from double-float exit times: t = (A - ph - pl) * (ih + il)
-        const int Ae = sel3(A, bs);
-        const float phe = sel3(ph, bs), ple = sel3(pl, bs);
-        const float ihe = sel3(d.ih, bs), ile = sel3(d.il, bs);
-        const float Af = __int2float_rn(Ae);
-        const float s = __fsub_rn(Af, phe);
-        const float bb = __fsub_rn(s, Af);
-        const float e1 = __fadd_rn(__fsub_rn(Af, __fsub_rn(s, bb)), __fsub_rn(-phe, bb));
-        const float rl = __fsub_rn(e1, ple);
-        const float th = __fmul_rn(s, ihe);
-        const float tl = __fadd_rn(__fmaf_rn(s, ihe, -th), __fmaf_rn(s, ile, __fmul_rn(rl, ihe)));
-        const float ds = __fmul_rn(__fadd_rn(__fsub_rn(th, tih), __fsub_rn(tl, til)), 0x1p-21f);
-        tih = th;
-        til = tl;
-        vis.seg((uint32_t)j, ds);
-        wc.nseg++;
-        // step the exit axes; leave at the domain edge
-        bool leaving = false;
-#pragma unroll
-        for (int b = 0; b < 3; b++) {
-            if (E & (1u << b)) {
-                if (d.flags & (8 << b)) {
-                    if (lo[b] + size >= t.ext[b]) leaving = true;
-                } else {
-                    if (lo[b] == 0) leaving = true;
-                }
-            }
-        }
-        if (leaving) break;
-        if (UNIFORM) {
-#pragma unroll
-            for (int b = 0; b < 3; b++) {
-                if (E & (1u << b)) {
-                    const uint32_t mb = kDilX << b;
-                    uint32_t db = dil & mb;
-                    if (d.flags & (8 << b)) { ci[b]++; db = ((db | ~mb) + (1u << b)) & mb; }
-                    else { ci[b]--; db = (db - (1u << b)) & mb; }
-                    dil = (dil & ~mb) | db;
-                }
-            }
-            j = dil;
-            continue;
-        }
-        // general octree: position of the non-stepped axes at t_out as a
-        // certified integer interval [clo, chi] (depth-21 cells)
-        uint32_t chi[3];
-        bool wide = false;
-#pragma unroll
-        for (int b = 0; b < 3; b++) {
-            const uint32_t lob = lo[b], hib = lo[b] + size - 1;
-            if (E & (1u << b)) {
-                c[b] = (d.flags & (8 << b)) ? lo[b] + size : lo[b] - 1;
-                chi[b] = c[b];
-            } else if (!(d.flags & (1 << b))) {
-                c[b] = min(max((uint32_t)qi[b], lob), hib);
-                chi[b] = c[b];
-            } else {
-                const float mw = __fmul_rn(th, d.m32[b]);
-                const float w = __fadd_rn(mw, ph[b]);
-                const float del = (fabsf(mw) + fabsf(w)) * 0x1p-21f +
-                                  fabsf(d.m32[b]) * fabsf(ihe) * 0x1p-22f + 0x1p-22f;
-                const long long l0 = (long long)qi[b] + (long long)floorf(__fsub_rd(w, del));
-                const long long l1 = (long long)qi[b] + (long long)floorf(__fadd_ru(w, del));
-                c[b] = (uint32_t)min(max(l0, (long long)lob), (long long)hib);
-                chi[b] = (uint32_t)min(max(l1, (long long)lob), (long long)hib);
-                if (chi[b] != c[b]) wide = true;
-            }
-        }
-        uint64_t key;
-        int level;
-        j = lookup_leaf(t, c[0], c[1], c[2], key, level);
-        if (j >= 0 && wide) {
-            uint32_t nlo[3], nsize;
-            leaf_box(key, level, nlo, nsize);
-#pragma unroll
-            for (int b = 0; b < 3; b++)
-                if (chi[b] >= nlo[b] + nsize) j = -2;  // the interval crosses a leaf face
-        }
-        if (j == -2 || (j < 0 && wide)) {
-            // FP64 position of the definition: P = Q + t_out m, floor(P 2^21)
-            wc.lookup_fb++;
-            const long long De = ((long long)Ae << 32) - (long long)sel3(qf, bs);
-            const double te = __dmul_rn(__dmul_rn(__ll2double_rn(De), 0x1p-53), sel3(d.inv, bs));
-#pragma unroll
-            for (int b = 0; b < 3; b++) {
-                if (!(E & (1u << b)) && (d.flags & (1 << b))) {
-                    const long long qb = ((long long)qi[b] << 32) | (long long)qf[b];
-                    const double Qb = __dmul_rn(__ll2double_rn(qb), 0x1p-53);
-                    const double P = __dadd_rn(Qb, __dmul_rn(te, d.m[b]));
-                    double f = floor(__dmul_rn(P, 0x1p21));
-                    f = fmax(f, (double)lo[b]);
-                    f = fmin(f, (double)(lo[b] + size - 1));
-                    c[b] = (uint32_t)f;
-                }
-            }
-            j = lookup_leaf(t, c[0], c[1], c[2], key, level);
-        }
-        if (j < 0) return RT_ERR_LOOKUP_MISS;
-        leaf_box(key, level, lo, size);
-    }
-    return RT_OK;
-}
+// In depth-21 units a source coordinate is qi + qf 2^-32 (qi integer, qf a
+// 32-bit fraction) and a face-minus-source distance is D 2^-32 with
+// D = (F - qi) 2^32 - qf an exact integer; the FP64 exit time of the
+// definition is fl(D 2^-53 inv) box lengths.  QZ marks a source whose
+// fractions are all zero (every leaf centre down to level 20): then ph = pl =
+// 0 and A = F - qi is the whole distance.
 
 // ------------------------------------ F32-Kahan walk on a uniform grid
 
 // Double-float exit time t = (A - ph - pl) * (ih + il) (depth-21 units) of one
 // axis: th = fl(fl(A - ph) * ih) is the FP32 time the certified bound is stated
 // for, th + tl carries about 44 bits.
+template <bool QZ>
 __device__ __forceinline__ void exit_time(float Af, float ph, float pl, float ih, float il, float& th,
                                           float& tl)
 {
+    if (QZ) {
+        th = __fmul_rn(Af, ih);
+        tl = __fmaf_rn(Af, il, __fmaf_rn(Af, ih, -th));
+        return;
+    }
     const float s = __fsub_rn(Af, ph);
     const float bb = __fsub_rn(s, Af);
     const float e1 = __fadd_rn(__fsub_rn(Af, __fsub_rn(s, bb)), __fsub_rn(-ph, bb));
     const float rl = __fsub_rn(e1, pl);
     th = __fmul_rn(s, ih);
     tl = __fadd_rn(__fmaf_rn(s, ih, -th), __fmaf_rn(s, il, __fmul_rn(rl, ih)));
+}
+
+// Integer value of an integer-valued float |v| < 2^22 without a conversion
+// instruction.
+__device__ __forceinline__ int small_float_to_int(float v)
+{
+    return __float_as_int(__fadd_rn(v, 12582912.0f)) - 0x4B400000;
+}
+
+// The smallest, second and third smallest FP32 exit times over the moving
+// axes VM, with the axes of the first two (ties: lower axis first).
+template <int VM>
+__device__ __forceinline__ void order_exits(const float th[3], float& t1, int& i1, float& t2, int& i2,
+                                            float& t3)
+{
+    const float inf = __int_as_float(0x7f800000);
+    if (VM == 7) {
+        const bool s = th[1] < th[0];
+        const float lo = s ? th[1] : th[0], hi = s ? th[0] : th[1];
+        const int il = s ? 1 : 0, ih = s ? 0 : 1;
+        if (th[2] < lo) { t1 = th[2]; i1 = 2; t2 = lo; i2 = il; t3 = hi; }
+        else if (th[2] < hi) { t1 = lo; i1 = il; t2 = th[2]; i2 = 2; t3 = hi; }
+        else { t1 = lo; i1 = il; t2 = hi; i2 = ih; t3 = th[2]; }
+    } else if (VM == 3 || VM == 5 || VM == 6) {
+        const int a = (VM == 6) ? 1 : 0, b = (VM == 3) ? 1 : 2;
+        const bool s = th[b] < th[a];
+        t1 = s ? th[b] : th[a]; i1 = s ? b : a;
+        t2 = s ? th[a] : th[b]; i2 = s ? a : b;
+        t3 = inf;
+    } else {
+        const int a = (VM == 1) ? 0 : (VM == 2 ? 1 : 2);
+        t1 = th[a]; i1 = a; t2 = t3 = inf; i2 = a;
+    }
 }
 
 // Exit set when the two smallest FP32 times are within the certified margin:
@@ -509,14 +345,14 @@ __device__ __forceinline__ unsigned resolve_exit(const float th[3], const float 
     unsigned E = 1u << bs;
     bool amb = false;
     const float tmin = sel3(th, bs);
-    const long long Ds = ((long long)__float2int_rn(sel3(Af, bs)) << 32) - (long long)sel3(qf, bs);
+    const long long Ds = ((long long)small_float_to_int(sel3(Af, bs)) << 32) - (long long)sel3(qf, bs);
     const float errs = fabsf(tmin) * kER + fabsf(sel3(ih, bs)) * kEA;
 #pragma unroll
     for (int b = 0; b < 3; b++) {
         if ((VM & (1 << b)) && b != bs) {
             const float errb = fabsf(th[b]) * kER + fabsf(ih[b]) * kEA;
             if (__fsub_rn(th[b], tmin) <= errs + errb) {
-                const long long Db = ((long long)__float2int_rn(Af[b]) << 32) - (long long)qf[b];
+                const long long Db = ((long long)small_float_to_int(Af[b]) << 32) - (long long)qf[b];
                 if (inv_equal(flags, b, bs) && llabs(Db) == llabs(Ds)) E |= 1u << b;
                 else amb = true;
             }
@@ -530,7 +366,7 @@ __device__ __forceinline__ unsigned resolve_exit(const float th[3], const float 
         for (int b = 0; b < 3; b++) {
             tb[b] = mn;
             if (VM & (1 << b)) {
-                const long long D = ((long long)__float2int_rn(Af[b]) << 32) - (long long)qf[b];
+                const long long D = ((long long)small_float_to_int(Af[b]) << 32) - (long long)qf[b];
                 tb[b] = __dmul_rn(__dmul_rn(__ll2double_rn(D), 0x1p-53), __ldg(&dp->inv[b]));
             }
         }
@@ -544,49 +380,88 @@ __device__ __forceinline__ unsigned resolve_exit(const float th[3], const float 
     return E;
 }
 
-// Walk of one ray through a full cube of equal-level leaves (level L <= 10),
-// F32-Kahan arithmetic, for a direction whose moving axes are the bits of VM.
-// The leaf index is the level-L Morton index, kept per axis in dilated form;
-// the per-axis far-face distance A (exact integer and exact float) and the
-// double-float exit time change only on the axes that step.
-template <int VM, class V>
-__device__ __forceinline__ int walk_f32k_grid(const DevTree& t, const DirConst* __restrict__ dp,
-                                              const double* __restrict__ src, long long cap, V& vis,
-                                              WalkCounters& wc)
+// Exit set of one step: the smallest exit time decides unless the second is
+// within the certified margin; then an exact tie of two equal-|inv| axes of a
+// QZ source is recognised from equal |A|, and anything else is resolved.
+template <int VM, bool QZ>
+__device__ __forceinline__ unsigned exit_set(const float th[3], const float Af[3], const uint32_t qf[3],
+                                             const float ih[3], int flags, float cE,
+                                             const DirConst* __restrict__ dp, int& bs, WalkCounters& wc)
 {
     constexpr int nvm = ((VM >> 0) & 1) + ((VM >> 1) & 1) + ((VM >> 2) & 1);
-    const int sh = kDepth - t.uniform_level;
-    const int N1 = (1 << t.uniform_level) - 1;
-    const int size = 1 << sh;
-    const int flags = __ldg(&dp->flags);
-    float ih[3], il[3];
-    uint32_t qf[3];
-    float ph[3], pl[3];
-    int c[3];
-    float Af[3], th[3], tl[3];
-    uint32_t dl[3];
-    float cE = 0.f;
+    float t1, t2, t3;
+    int i1, i2;
+    order_exits<VM>(th, t1, i1, t2, i2, t3);
+    bs = i1;
+    unsigned E = 1u << i1;
+    if (nvm > 1 && !(__fsub_rn(t2, t1) > (fabsf(t2) + fabsf(t1)) * kER + 2.f * cE)) {
+        bool done = false;
+        if (QZ && t2 == t1 && inv_equal(flags, i1, i2) && fabsf(sel3(Af, i1)) == fabsf(sel3(Af, i2)) &&
+            (nvm < 3 || __fsub_rn(t3, t1) > (fabsf(t3) + fabsf(t1)) * kER + 2.f * cE)) {
+            E |= 1u << i2;
+            bs = min(i1, i2);
+            done = true;
+        }
+        if (!done) {
+            E = resolve_exit<VM>(th, Af, qf, ih, flags, dp, i1, wc);
+            bs = __ffs(E) - 1;
+        }
+    }
+    return E;
+}
+
+// Source coordinates on the 2^-53 lattice: qi + qf 2^-32 (depth-21 units) and
+// the exact split qf 2^-32 = ph + pl.
+__device__ __forceinline__ int source_fixed(const double* __restrict__ src, const DevTree& t, int qi[3],
+                                            uint32_t qf[3], float ph[3], float pl[3])
+{
 #pragma unroll
     for (int b = 0; b < 3; b++) {
         long long q;
         if (!fixed_source(src[b], q)) return RT_ERR_SOURCE_OUTSIDE;
-        const int qi = (int)(q >> 32);
+        qi[b] = (int)(q >> 32);
         qf[b] = (uint32_t)(q & 0xffffffffll);
-        if ((uint32_t)qi >= t.ext[b]) return RT_ERR_SOURCE_OUTSIDE;
+        if ((uint32_t)qi[b] >= t.ext[b]) return RT_ERR_SOURCE_OUTSIDE;
         const float fh = __uint2float_rn(qf[b]);
         const long long back = (long long)__float2ull_rz(fh);
         ph[b] = fh * 0x1p-32f;
         pl[b] = __ll2float_rn((long long)qf[b] - back) * 0x1p-32f;
-        c[b] = qi >> sh;
+    }
+    return RT_OK;
+}
+
+// Walk of one ray through a full cube of equal-level leaves (level L <= 10),
+// F32-Kahan arithmetic, for a direction whose moving axes are the bits of VM.
+// The leaf index is the level-L Morton index, kept per axis in dilated form;
+// the per-axis far-face distance A (an exact float) and the double-float exit
+// time change only on the axes that step.
+template <int VM, bool QZ, class V>
+__device__ __forceinline__ int walk_f32k_grid(const DevTree& t, const DirConst* __restrict__ dp,
+                                              const double* __restrict__ src, long long cap, V& vis,
+                                              WalkCounters& wc)
+{
+    const int sh = kDepth - t.uniform_level;
+    const int N1 = (1 << t.uniform_level) - 1;
+    const int size = 1 << sh;
+    const int flags = __ldg(&dp->flags);
+    float ih[3], il[3], ph[3], pl[3];
+    int qi[3], c[3];
+    uint32_t qf[3], dl[3];
+    float Af[3], th[3], tl[3];
+    float cE = 0.f;
+    const int st = source_fixed(src, t, qi, qf, ph, pl);
+    if (st != RT_OK) return st;
+#pragma unroll
+    for (int b = 0; b < 3; b++) {
+        c[b] = qi[b] >> sh;
         dl[b] = spread10((uint32_t)c[b]) << b;
-        Af[b] = 0.f;
-        th[b] = tl[b] = ih[b] = il[b] = 0.f;
+        Af[b] = th[b] = tl[b] = ih[b] = il[b] = 0.f;
         if (VM & (1 << b)) {
             ih[b] = __ldg(&dp->ih[b]);
             il[b] = __ldg(&dp->il[b]);
             const int pos = (flags >> (3 + b)) & 1;
-            Af[b] = __int2float_rn(((c[b] + pos) << sh) - qi);
-            exit_time(Af[b], ph[b], pl[b], ih[b], il[b], th[b], tl[b]);
+            Af[b] = __int2float_rn(((c[b] + pos) << sh) - qi[b]);
+            exit_time<QZ>(Af[b], ph[b], pl[b], ih[b], il[b], th[b], tl[b]);
             cE = fmaxf(cE, fabsf(ih[b]) * kEA);
         }
     }
@@ -595,20 +470,8 @@ __device__ __forceinline__ int walk_f32k_grid(const DevTree& t, const DirConst* 
     for (long long step = 0;; ++step) {
         if (step >= cap) return RT_ERR_STEP_LIMIT;
         vis.pre(j);
-        float tmin = __int_as_float(0x7f800000), t2 = tmin;
-        int bs = 0;
-#pragma unroll
-        for (int b = 0; b < 3; b++) {
-            if (VM & (1 << b)) {
-                if (th[b] < tmin) { t2 = tmin; tmin = th[b]; bs = b; }
-                else t2 = fminf(t2, th[b]);
-            }
-        }
-        unsigned E = 1u << bs;
-        if (nvm > 1 && !(__fsub_rn(t2, tmin) > (fabsf(t2) + fabsf(tmin)) * kER + 2.f * cE)) {
-            E = resolve_exit<VM>(th, Af, qf, ih, flags, dp, bs, wc);
-            bs = __ffs(E) - 1;
-        }
+        int bs;
+        const unsigned E = exit_set<VM, QZ>(th, Af, qf, ih, flags, cE, dp, bs, wc);
         const float ths = sel3(th, bs), tls = sel3(tl, bs);
         const float ds = __fmul_rn(__fadd_rn(__fsub_rn(ths, tih), __fsub_rn(tls, til)), 0x1p-21f);
         tih = ths;
@@ -623,7 +486,7 @@ __device__ __forceinline__ int walk_f32k_grid(const DevTree& t, const DirConst* 
                 if (c[b] == (pos ? N1 : 0)) leaving = true;
                 c[b] += pos ? 1 : -1;
                 Af[b] = __fadd_rn(Af[b], pos ? (float)size : -(float)size);
-                exit_time(Af[b], ph[b], pl[b], ih[b], il[b], th[b], tl[b]);
+                exit_time<QZ>(Af[b], ph[b], pl[b], ih[b], il[b], th[b], tl[b]);
                 const uint32_t mb = kDilX << b;
                 dl[b] = pos ? (((dl[b] | ~mb) + (1u << b)) & mb) : ((dl[b] - (1u << b)) & mb);
             }
@@ -632,6 +495,222 @@ __device__ __forceinline__ int walk_f32k_grid(const DevTree& t, const DirConst* 
         j = dl[0] | dl[1] | dl[2];
     }
     return RT_OK;
+}
+
+// ------------------------------------ F32-Kahan walk on a general octree
+
+// Exact float of an integer 0 <= v < 2^23 without a conversion instruction.
+__device__ __forceinline__ float small_int_to_float(uint32_t v)
+{
+    return __fsub_rn(__int_as_float(0x4B000000 | (int)v), 8388608.0f);
+}
+
+// Leaf containing the depth-21 point c, and its level.  The coarse table gives
+// the leaf directly for a coarse cell inside one leaf or of one level (no key
+// or level is read then); a mixed cell is searched by key.  -1: no leaf.
+__device__ __forceinline__ long long find_leaf(const DevTree& t, const uint32_t c[3], int& level)
+{
+    const int s = kDepth - t.T;
+    const uint32_t cell = spread10(c[0] >> s) | (spread10(c[1] >> s) << 1) | (spread10(c[2] >> s) << 2);
+    const uint64_t e = __ldg(t.table + cell);
+    const int code = (int)(e & 63u);
+    const long long first = (long long)(e >> 6);
+    if (code <= t.T) {
+        level = code;
+        return first;
+    }
+    if (code <= kDepth) {
+        const int sl = kDepth - code;
+        const uint32_t mask = (1u << (code - t.T)) - 1u;
+        const uint64_t local = spread21((c[0] >> sl) & mask) | (spread21((c[1] >> sl) & mask) << 1) |
+                               (spread21((c[2] >> sl) & mask) << 2);
+        level = code;
+        return first + (long long)local;
+    }
+    if (code == kCodeHole) return -1;
+    const uint64_t M = interleave3(c[0], c[1], c[2]);
+    const uint64_t ncell = 1ull << (3 * t.T);
+    long long hi = ((uint64_t)cell + 1 < ncell) ? (long long)(__ldg(t.table + cell + 1) >> 6) : t.n;
+    long long lo = first;  // keys[lo] == cell base <= M
+    while (hi - lo > 1) {
+        const long long mid = (lo + hi) >> 1;
+        if (__ldg(t.keys + mid) <= M) lo = mid;
+        else hi = mid;
+    }
+    const uint64_t key = __ldg(t.keys + lo);
+    level = __ldg(t.levels + lo);
+    if (M - key >= (1ull << (3 * (kDepth - level)))) return -1;
+    return lo;
+}
+
+// Walk of one ray through a general octree, F32-Kahan arithmetic, moving axes
+// VM (compile time).  Exit decisions as in walk_f32k_grid; the next leaf is
+// looked up at the FP32 position of the non-stepped axes when its certified
+// interval lies inside the leaf found, else at the FP64 position.
+template <int VM, bool QZ, class V>
+__device__ __forceinline__ int walk_f32k_tree(const DevTree& t, const DirConst* __restrict__ dp,
+                                              const double* __restrict__ src, long long cap, V& vis,
+                                              WalkCounters& wc)
+{
+    const int flags = __ldg(&dp->flags);
+    float ih[3], il[3], m32[3], ph[3], pl[3], qif[3];
+    int qi[3];
+    uint32_t qf[3], c[3];
+    float cE = 0.f;
+    const int st = source_fixed(src, t, qi, qf, ph, pl);
+    if (st != RT_OK) return st;
+#pragma unroll
+    for (int b = 0; b < 3; b++) {
+        qif[b] = small_int_to_float((uint32_t)qi[b]);
+        c[b] = (uint32_t)qi[b];
+        ih[b] = il[b] = m32[b] = 0.f;
+        if (VM & (1 << b)) {
+            ih[b] = __ldg(&dp->ih[b]);
+            il[b] = __ldg(&dp->il[b]);
+            m32[b] = __ldg(&dp->m32[b]);
+            cE = fmaxf(cE, fabsf(ih[b]) * kEA);
+        }
+    }
+    int level;
+    long long j = find_leaf(t, c, level);
+    if (j < 0) return RT_ERR_LOOKUP_MISS;
+    uint32_t size = 1u << (kDepth - level);
+    uint32_t lo[3];
+#pragma unroll
+    for (int b = 0; b < 3; b++) lo[b] = c[b] & ~(size - 1u);
+    float tih = 0.f, til = 0.f;
+    for (long long step = 0;; ++step) {
+        if (step >= cap) return RT_ERR_STEP_LIMIT;
+        vis.pre((uint32_t)j);
+        float Af[3], th[3], tl[3];
+#pragma unroll
+        for (int b = 0; b < 3; b++) {
+            Af[b] = th[b] = tl[b] = 0.f;
+            if (VM & (1 << b)) {
+                const uint32_t F = ((flags >> (3 + b)) & 1) ? lo[b] + size : lo[b];
+                Af[b] = __fsub_rn(small_int_to_float(F), qif[b]);
+                if (QZ) {
+                    th[b] = __fmul_rn(Af[b], ih[b]);
+                } else {
+                    th[b] = __fmul_rn(__fsub_rn(Af[b], ph[b]), ih[b]);
+                }
+            }
+        }
+        int bs;
+        const unsigned E = exit_set<VM, QZ>(th, Af, qf, ih, flags, cE, dp, bs, wc);
+        float the, tle;
+        exit_time<QZ>(sel3(Af, bs), sel3(ph, bs), sel3(pl, bs), sel3(ih, bs), sel3(il, bs), the, tle);
+        const float ds = __fmul_rn(__fadd_rn(__fsub_rn(the, tih), __fsub_rn(tle, til)), 0x1p-21f);
+        tih = the;
+        til = tle;
+        vis.acc(ds);
+        wc.nseg++;
+        // step the exit axes, position the others on a certified interval
+        const float ihe = sel3(ih, bs);
+        bool leaving = false, wide = false;
+        uint32_t chi[3];
+#pragma unroll
+        for (int b = 0; b < 3; b++) {
+            const int pos = (flags >> (3 + b)) & 1;
+            if ((VM & (1 << b)) && (E & (1u << b))) {
+                if (pos ? (lo[b] + size >= t.ext[b]) : (lo[b] == 0)) leaving = true;
+                c[b] = pos ? lo[b] + size : lo[b] - 1;
+                chi[b] = c[b];
+            } else if (!(VM & (1 << b))) {
+                c[b] = (uint32_t)qi[b];  // a fixed coordinate stays inside every leaf on the path
+                chi[b] = c[b];
+            } else {
+                const uint32_t hib = lo[b] + size - 1;
+                const float mw = __fmul_rn(the, m32[b]);
+                const float w = QZ ? mw : __fadd_rn(mw, ph[b]);
+                const float del = (fabsf(mw) + fabsf(w)) * 0x1p-21f + fabsf(m32[b]) * fabsf(ihe) * 0x1p-22f +
+                                  0x1p-22f;
+                const long long l0 = (long long)qi[b] + (long long)floorf(__fsub_rd(w, del));
+                const long long l1 = (long long)qi[b] + (long long)floorf(__fadd_ru(w, del));
+                c[b] = (uint32_t)min(max(l0, (long long)lo[b]), (long long)hib);
+                chi[b] = (uint32_t)min(max(l1, (long long)lo[b]), (long long)hib);
+                wide |= chi[b] != c[b];
+            }
+        }
+        if (leaving) break;
+        const uint32_t size0 = size;  // the current leaf's size
+        j = find_leaf(t, c, level);
+        size = 1u << (kDepth - level);
+        if (wide && j >= 0) {
+#pragma unroll
+            for (int b = 0; b < 3; b++)
+                if (chi[b] >= (c[b] & ~(size - 1u)) + size) j = -2;
+        }
+        if (j == -2 || (j < 0 && wide)) {
+            // FP64 position of the definition: floor((Q + t_out m) 2^21)
+            wc.lookup_fb++;
+            const long long De = ((long long)small_float_to_int(sel3(Af, bs)) << 32) - (long long)sel3(qf, bs);
+            const double te = __dmul_rn(__dmul_rn(__ll2double_rn(De), 0x1p-53), __ldg(&dp->inv[bs]));
+#pragma unroll
+            for (int b = 0; b < 3; b++) {
+                if ((VM & (1 << b)) && !(E & (1u << b))) {
+                    const long long qb = ((long long)qi[b] << 32) | (long long)qf[b];
+                    const double Qb = __dmul_rn(__ll2double_rn(qb), 0x1p-53);
+                    const double P = __dadd_rn(Qb, __dmul_rn(te, __ldg(&dp->m[b])));
+                    double f = floor(__dmul_rn(P, 0x1p21));
+                    f = fmax(f, (double)lo[b]);
+                    f = fmin(f, (double)(lo[b] + size0 - 1));
+                    c[b] = (uint32_t)f;
+                }
+            }
+            j = find_leaf(t, c, level);
+            size = 1u << (kDepth - level);
+        }
+        if (j < 0) return RT_ERR_LOOKUP_MISS;
+#pragma unroll
+        for (int b = 0; b < 3; b++) lo[b] = c[b] & ~(size - 1u);
+    }
+    return RT_OK;
+}
+
+// True when every coordinate of the source has a zero 32-bit fraction on the
+// depth-21 lattice (every leaf centre down to level 20 does).
+__device__ __forceinline__ bool source_on_lattice(const double* __restrict__ src)
+{
+    bool z = true;
+#pragma unroll
+    for (int b = 0; b < 3; b++) {
+        long long q;
+        if (fixed_source(src[b], q)) z = z && ((q & 0xffffffffll) == 0);
+    }
+    return z;
+}
+
+template <bool QZ, class V>
+__device__ __forceinline__ int walk_grid_vm(int vm, const DevTree& t, const DirConst* __restrict__ dp,
+                                            const double* __restrict__ src, long long cap, V& vis,
+                                            WalkCounters& wc)
+{
+    switch (vm) {
+    case 1: return walk_f32k_grid<1, QZ>(t, dp, src, cap, vis, wc);
+    case 2: return walk_f32k_grid<2, QZ>(t, dp, src, cap, vis, wc);
+    case 3: return walk_f32k_grid<3, QZ>(t, dp, src, cap, vis, wc);
+    case 4: return walk_f32k_grid<4, QZ>(t, dp, src, cap, vis, wc);
+    case 5: return walk_f32k_grid<5, QZ>(t, dp, src, cap, vis, wc);
+    case 6: return walk_f32k_grid<6, QZ>(t, dp, src, cap, vis, wc);
+    default: return walk_f32k_grid<7, QZ>(t, dp, src, cap, vis, wc);
+    }
+}
+
+template <bool QZ, class V>
+__device__ __forceinline__ int walk_tree_vm(int vm, const DevTree& t, const DirConst* __restrict__ dp,
+                                            const double* __restrict__ src, long long cap, V& vis,
+                                            WalkCounters& wc)
+{
+    switch (vm) {
+    case 1: return walk_f32k_tree<1, QZ>(t, dp, src, cap, vis, wc);
+    case 2: return walk_f32k_tree<2, QZ>(t, dp, src, cap, vis, wc);
+    case 3: return walk_f32k_tree<3, QZ>(t, dp, src, cap, vis, wc);
+    case 4: return walk_f32k_tree<4, QZ>(t, dp, src, cap, vis, wc);
+    case 5: return walk_f32k_tree<5, QZ>(t, dp, src, cap, vis, wc);
+    case 6: return walk_f32k_tree<6, QZ>(t, dp, src, cap, vis, wc);
+    default: return walk_f32k_tree<7, QZ>(t, dp, src, cap, vis, wc);
+    }
 }
 
 // Walk of one ray (direction *dp, in global memory) in either arithmetic form.
@@ -644,19 +723,11 @@ __device__ __forceinline__ int walk(const DevTree& t, const DirConst* __restrict
         const DirConst d = *dp;
         return walk_fp64<UNIFORM>(t, d, src, cap, vis, wc);
     }
-    if (UNIFORM) {
-        switch (__ldg(&dp->flags) & 7) {
-        case 1: return walk_f32k_grid<1>(t, dp, src, cap, vis, wc);
-        case 2: return walk_f32k_grid<2>(t, dp, src, cap, vis, wc);
-        case 3: return walk_f32k_grid<3>(t, dp, src, cap, vis, wc);
-        case 4: return walk_f32k_grid<4>(t, dp, src, cap, vis, wc);
-        case 5: return walk_f32k_grid<5>(t, dp, src, cap, vis, wc);
-        case 6: return walk_f32k_grid<6>(t, dp, src, cap, vis, wc);
-        default: return walk_f32k_grid<7>(t, dp, src, cap, vis, wc);
-        }
-    }
-    const DirConst d = *dp;
-    return walk_f32k<UNIFORM>(t, d, src, cap, vis, wc);
+    const int vm = __ldg(&dp->flags) & 7;
+    const bool qz = source_on_lattice(src);
+    if (UNIFORM)
+        return qz ? walk_grid_vm<true>(vm, t, dp, src, cap, vis, wc) : walk_grid_vm<false>(vm, t, dp, src, cap, vis, wc);
+    return qz ? walk_tree_vm<true>(vm, t, dp, src, cap, vis, wc) : walk_tree_vm<false>(vm, t, dp, src, cap, vis, wc);
 }
 
 // ------------------------------------------------------------- densities

@@ -8,8 +8,14 @@
 
 #include "rt_device.cuh"
 
+// Resident 256-thread blocks per SM the register budget is sized for: the
+// uniform-grid F32-Kahan walk runs best at 64 registers (4 blocks), the
+// others keep the compiler's choice.
+#ifndef RT_MIN_BLOCKS_GRID
+#define RT_MIN_BLOCKS_GRID 4
+#endif
 #ifndef RT_MIN_BLOCKS
-#define RT_MIN_BLOCKS 1  // resident 256-thread blocks per SM the register budget is sized for
+#define RT_MIN_BLOCKS 1
 #endif
 
 namespace rt {
@@ -122,7 +128,8 @@ __device__ __forceinline__ void flush_counters(DevStats* st, unsigned long long 
 
 // KIND 0: forward columns; 1: path fingerprints; 2: adjoint scatter.
 template <int KIND, int MODE, bool UNIFORM, int SM>
-__global__ void __launch_bounds__(256, RT_MIN_BLOCKS) k_trace(const TraceArgs a)
+__global__ void __launch_bounds__(256, (MODE == RT_MODE_F32_KAHAN && UNIFORM) ? RT_MIN_BLOCKS_GRID : RT_MIN_BLOCKS)
+k_trace(const TraceArgs a)
 {
     const int lane = threadIdx.x & 31;
     const unsigned long long total = (unsigned long long)a.n_src_pad * (unsigned long long)a.nd;
