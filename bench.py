@@ -41,6 +41,9 @@ def parse():
     p.add_argument("--level", type=int, default=LEVEL, help="uniform grid level (9 = 512^3)")
     p.add_argument("--no-extras", action="store_true", help="skip FP64 form, adjoint, e2e, CPU baseline")
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
+    p.add_argument("--workload", default="uniform512",
+                   choices=["uniform512", "amr128", "batched64", "adjoint_amr64"],
+                   help="uniform512 is the benchmark; the others run one secondary workload alone")
     return p.parse_args()
 
 
@@ -184,7 +187,7 @@ def timed(fn, stream, reps=1):
     return e0.elapsed_time(e1) / 1e3 / reps
 
 
-def amr_leg(rt, dev, stream, check_sources=400):
+def amr_leg(rt, dev, stream, check_sources=400, reps=3):
     """AMR workload: 128^3 base (sigma 1.5), field on 512^3, 2 levels above p90,
     4 FP32 species, 1M mass-weighted sources, Nside 2, F32-Kahan; plus an
     oracle spot check of a few hundred sources."""
@@ -195,10 +198,10 @@ def amr_leg(rt, dev, stream, check_sources=400):
     tree = rt.Octree(keys, lev, extent=ext)
     out = torch.empty((src.shape[0], 48, 4), dtype=torch.float32, device=dev)
     tree.reset_stats()
-    t = timed(lambda: rt.trace_columns(tree, src, 2, dens, "f32k", out=out), stream, reps=3)
+    t = timed(lambda: rt.trace_columns(tree, src, 2, dens, "f32k", out=out), stream, reps=reps)
     st = tree.stats()
     assert st["status"] == 0, st
-    segs = st["segments"] / 4
+    segs = st["segments"] / (reps + 1)
     res = {"workload": "128^3 base AMR (2 levels above p90, %d leaves), 4 FP32 species, 1M mass-weighted "
                        "sources, Nside 2, F32-Kahan" % keys.numel(),
            "value": segs / t, "unit": "ray-segments/s", "ms_per_step": t * 1e3,
@@ -216,7 +219,7 @@ def amr_leg(rt, dev, stream, check_sources=400):
     return res
 
 
-def batched_leg(rt, dev, stream, cache):
+def batched_leg(rt, dev, stream, cache, reps=3):
     """64 independent clouds (base in {16,24,32,48,64,96}^3, 0-3 levels above
     p80, 2 FP32 species, leaf-centre sources, Nside 1 or 2) in one launch,
     launch shape from the autotuner."""
@@ -236,12 +239,12 @@ def batched_leg(rt, dev, stream, cache):
     batch = rt.Batch(clouds, "f32k")
     best, rate = batch.autotune(cache)
     batch.reset_stats()
-    t = timed(lambda: batch.launch(), stream, reps=3)
+    t = timed(lambda: batch.launch(), stream, reps=reps)
     st = batch.stats()
     assert st["status"] == 0, st
-    segs = st["segments"] / 4
+    segs = st["segments"] / (reps + 1)
     res = {"workload": "64 clouds of uneven size and depth, %d rays, one persistent launch (CUDA graph)"
-                       % (st["rays"] // 4),
+                       % (st["rays"] // (reps + 1)),
            "value": segs / t, "unit": "ray-segments/s", "ms_per_step": t * 1e3,
            "autotuned": {"threads": best[0], "blocks_per_sm": best[1], "groups_per_pop": best[2]}}
     batch.close()
@@ -251,7 +254,7 @@ def batched_leg(rt, dev, stream, cache):
     return res
 
 
-def adjoint_leg(rt, dev, stream):
+def adjoint_leg(rt, dev, stream, reps=3):
     """Differentiable workload: 64^3 base refined once above p85, one species,
     leaf-centre sources, Nside 2: forward (F32-Kahan) and adjoint times."""
     import torch
@@ -260,10 +263,10 @@ def adjoint_leg(rt, dev, stream):
     tree = rt.Octree(k, l, extent=ext)
     src = torchgen.leaf_centres(k, l)
     out = torch.empty((src.shape[0], 48, 1), dtype=torch.float32, device=dev)
-    tf = timed(lambda: rt.trace_columns(tree, src, 2, d, "f32k", out=out), stream, reps=3)
+    tf = timed(lambda: rt.trace_columns(tree, src, 2, d, "f32k", out=out), stream, reps=reps)
     g = torch.rand_like(out)
     grad = torch.zeros((k.numel(), 1), dtype=torch.float64, device=dev)
-    ta = timed(lambda: rt.trace_columns_adjoint(tree, src, 2, g, "f32k", grad_dens=grad), stream, reps=3)
+    ta = timed(lambda: rt.trace_columns_adjoint(tree, src, 2, g, "f32k", grad_dens=grad), stream, reps=reps)
     tree.close()
     return {"workload": "64^3 base AMR, 1 level above p85 (%d leaves), 1 species, leaf-centre sources, Nside 2"
                         % k.numel(), "forward_ms": tf * 1e3, "adjoint_ms": ta * 1e3,
@@ -330,6 +333,17 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
+    if a.workload != "uniform512":
+        if a.workload == "amr128":
+            r = amr_leg(rt, dev, stream, reps=a.steps)
+        elif a.workload == "batched64":
+            r = batched_leg(rt, dev, stream, os.path.join(ROOT, "paper_2605_09882_gb300", "autotune_gb300.json"),
+                            reps=a.steps)
+        else:
+            r = adjoint_leg(rt, dev, stream, reps=a.steps)
+        if rank == 0:
+            print(json.dumps({"workload_only": a.workload, "steps": a.steps, **r}), flush=True)
+        return 0
     L = a.level
     n_side_cells = 1 << L
 

@@ -10,7 +10,8 @@ namespace rt {
 
 constexpr int kDepth = 21;          // anchor depth of the Morton lattice
 constexpr int kMaxSpecies = 8;
-constexpr int kMaxTableLevel = 7;   // coarse table: at most 8^7 = 2M entries
+constexpr int kBaseTableLevel = 7;  // coarse table level for every tree (8^7 = 2M entries at most)
+constexpr int kMaxTableLevel = 10;  // deepest coarse table (the lookup's cell index holds 30 bits)
 constexpr int kCodeHole = 62;       // coarse cell outside the domain box
 constexpr int kCodeMixed = 63;      // coarse cell with leaves of several levels
 

@@ -14,6 +14,9 @@
 #ifndef RT_MIN_BLOCKS_GRID
 #define RT_MIN_BLOCKS_GRID 4
 #endif
+#ifndef RT_MIN_BLOCKS_TREE
+#define RT_MIN_BLOCKS_TREE 1
+#endif
 #ifndef RT_MIN_BLOCKS
 #define RT_MIN_BLOCKS 1
 #endif
@@ -128,7 +131,8 @@ __device__ __forceinline__ void flush_counters(DevStats* st, unsigned long long 
 
 // KIND 0: forward columns; 1: path fingerprints; 2: adjoint scatter.
 template <int KIND, int MODE, bool UNIFORM, int SM>
-__global__ void __launch_bounds__(256, (MODE == RT_MODE_F32_KAHAN && UNIFORM) ? RT_MIN_BLOCKS_GRID : RT_MIN_BLOCKS)
+__global__ void __launch_bounds__(256, (MODE == RT_MODE_F32_KAHAN) ? (UNIFORM ? RT_MIN_BLOCKS_GRID : RT_MIN_BLOCKS_TREE)
+                                                                : RT_MIN_BLOCKS)
 k_trace(const TraceArgs a)
 {
     const int lane = threadIdx.x & 31;

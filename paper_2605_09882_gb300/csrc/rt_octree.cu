@@ -174,7 +174,16 @@ extern "C" int rt_build_octree(const uint64_t* d_keys, const uint8_t* d_levels, 
     if (status != RT_OK) goto fail;
     {
         const int lmax = (int)hv.lmax, lmin = (int)hv.lmin;
-        const int T = std::min(lmax, kMaxTableLevel);
+        const bool full = ext[0] == (1u << kDepth) && ext[1] == (1u << kDepth) && ext[2] == (1u << kDepth);
+        const bool uniform = lmin == lmax && lmax <= 10 && full && n_leaves == (int64_t)(1ll << (3 * lmax));
+        // Coarse table level: deep enough that most lookups are one table read
+        // (at lmax - 1 no coarse cell mixes levels), within 8 entries per leaf
+        // (never less than 8^7); a uniform cube uses the O(1) index instead.
+        int T = std::min(lmax, kBaseTableLevel);
+        if (!uniform) {
+            const uint64_t budget = std::max<uint64_t>(1ull << (3 * kBaseTableLevel), 8ull * (uint64_t)n_leaves);
+            while (T < std::min(lmax, kMaxTableLevel) && (1ull << (3 * (T + 1))) <= budget) T++;
+        }
         const uint64_t ncell = 1ull << (3 * T);
         if (cudaMalloc(&t->table, ncell * sizeof(uint64_t)) != cudaSuccess ||
             cudaMalloc(&lvmin, ncell * sizeof(unsigned)) != cudaSuccess ||
@@ -203,8 +212,7 @@ extern "C" int rt_build_octree(const uint64_t* d_keys, const uint8_t* d_levels, 
         for (int b = 0; b < 3; b++) d.ext[b] = ext[b];
         d.T = T;
         d.lmax = lmax;
-        const bool full = ext[0] == (1u << kDepth) && ext[1] == (1u << kDepth) && ext[2] == (1u << kDepth);
-        d.uniform_level = (lmin == lmax && lmax <= 10 && full && n_leaves == (int64_t)(1ll << (3 * lmax))) ? lmax : -1;
+        d.uniform_level = uniform ? lmax : -1;
         t->uniform_allowed = 1;
         t->default_cap = 3 * (1ll << lmax) + 3;
         d.step_cap = t->default_cap;
