@@ -139,11 +139,44 @@ int rt_trace_paths(const rt_octree* tree, const double* d_src, int64_t n_src, in
  *     RT_MODE_F32_KAHAN, float64 for RT_MODE_FP64.
  *   d_grad_dens: float64 [n_leaves][n_species], ACCUMULATED into (the caller
  *     zeroes it); summation order across rays is not fixed.
- *   path_policy: 0 = automatic, 1 = recompute the paths (the only policy
- *     implemented; 2 = record is rejected with RT_ERR_ARG). */
+ *   path_policy: 0 = automatic (recompute), 1 = recompute the paths while
+ *     scattering, 2 = record the paths (rt_record_paths), scatter from the
+ *     record and free it (synchronizes `stream`, resets the octree's
+ *     statistics).  To reuse a record, call rt_record_paths once and
+ *     rt_paths_adjoint / rt_paths_columns many times. */
 int rt_trace_columns_adjoint(const rt_octree* tree, const double* d_src, int64_t n_src,
                              int nside, const void* d_grad_out, int n_species, int mode,
                              double* d_grad_dens, int path_policy, void* stream);
+
+/* ---------------------------------------------------------- recorded paths
+ * The (leaf, ds) sequence of every ray, recorded once so that the forward
+ * columns and the adjoint can be evaluated again without walking (an
+ * addition of this library).  Rays are stored 32 at a time as the walk visits
+ * them: segment k of lane i of group g at slot off[g] + 32 k + i; a group
+ * holds 32 x its longest path.  About 8 bytes per slot in F32-Kahan mode (a
+ * uint32 leaf and a float32 ds), 12 in FP64 mode (float64 ds). */
+typedef struct rt_paths rt_paths; /* opaque */
+
+/* Walks every ray twice on `stream`: once to count the segments (then one
+ * synchronization to size the record) and once to write it.  Resets the
+ * octree's statistics.  RT_ERR_OOM if the record does not fit. */
+int rt_record_paths(const rt_octree* tree, const double* d_src, int64_t n_src, int nside, int mode,
+                    void* stream, rt_paths** out);
+
+/* Rays, segments and device bytes of a record. */
+int rt_paths_info(const rt_paths* paths, int64_t* n_rays, int64_t* n_segments, int64_t* bytes);
+
+/* Columns from a record, in the record's mode; the same arithmetic in the
+ * same order as rt_trace_columns, hence the same bits. */
+int rt_paths_columns(const rt_paths* paths, const void* d_dens, int n_species, int dens_dtype,
+                     void* d_out, void* stream);
+
+/* Adjoint from a record: d_grad_dens[j,k] += sum g[s,q,k] ds (accumulated). */
+int rt_paths_adjoint(const rt_paths* paths, const void* d_grad_out, int n_species,
+                     double* d_grad_dens, void* stream);
+
+/* Frees a record (synchronizes the device first).  NULL is ignored. */
+void rt_destroy_paths(rt_paths* paths);
 
 /* Copies the statistics of `tree` into *h_out after synchronizing `stream`. */
 int rt_get_stats(const rt_octree* tree, rt_stats* h_out, void* stream);

@@ -14,7 +14,7 @@ import numpy as np
 
 from . import _build
 
-__all__ = ["Octree", "Batch", "healpix_dirs", "trace_columns", "trace_paths", "trace_columns_adjoint",
+__all__ = ["Octree", "Batch", "Paths", "healpix_dirs", "trace_columns", "trace_paths", "trace_columns_adjoint",
            "Columns", "RTError", "MODE_FP64", "MODE_F32_KAHAN", "set_launch", "lib_path"]
 
 MODE_FP64, MODE_F32_KAHAN = 0, 1
@@ -74,6 +74,12 @@ def _load():
     lib.rt_batch_destroy.argtypes = [P]
     lib.rt_batch_destroy.restype = None
     lib.rt_autotune.argtypes = [P, C.c_char_p, C.POINTER(C.c_int * 3), C.POINTER(C.c_double), P]
+    lib.rt_record_paths.argtypes = [P, P, i64, i32, i32, P, C.POINTER(P)]
+    lib.rt_paths_info.argtypes = [P, C.POINTER(i64), C.POINTER(i64), C.POINTER(i64)]
+    lib.rt_paths_columns.argtypes = [P, P, i32, i32, P, P]
+    lib.rt_paths_adjoint.argtypes = [P, P, i32, P, P]
+    lib.rt_destroy_paths.argtypes = [P]
+    lib.rt_destroy_paths.restype = None
     return lib
 
 
@@ -213,8 +219,61 @@ def trace_paths(tree: Octree, src, nside: int, mode="f32k", stream=None):
     return nseg, hsh
 
 
+class Paths:
+    """Recorded (leaf, ds) sequences of every ray of (tree, src, nside, mode);
+    columns and adjoints are then evaluated without walking."""
+
+    def __init__(self, tree: Octree, src, nside: int, mode="f32k", stream=None):
+        self.mode = _mode(mode)
+        self.src = _check_src(src)
+        self.nside, self.tree = nside, tree
+        h = C.c_void_p()
+        _check(_lib.rt_record_paths(tree.handle, _dptr(self.src), int(self.src.shape[0]), int(nside), self.mode,
+                                    _stream(stream), C.byref(h)))
+        self._h = h
+
+    def info(self) -> dict:
+        r, s, b = C.c_int64(), C.c_int64(), C.c_int64()
+        _check(_lib.rt_paths_info(self._h, C.byref(r), C.byref(s), C.byref(b)))
+        return {"rays": r.value, "segments": s.value, "bytes": b.value}
+
+    def columns(self, dens, out=None, stream=None):
+        import torch
+        dens = dens.contiguous()
+        if dens.dim() == 1:
+            dens = dens[:, None]
+        S = int(dens.shape[1])
+        odt = torch.float32 if self.mode == MODE_F32_KAHAN else torch.float64
+        if out is None:
+            out = torch.empty((self.src.shape[0], 12 * self.nside ** 2, S), dtype=odt, device=dens.device)
+        _check(_lib.rt_paths_columns(self._h, _dptr(dens), S, F64 if dens.dtype == torch.float64 else F32,
+                                     _dptr(out), _stream(stream)))
+        return out
+
+    def adjoint(self, grad_out, grad_dens=None, stream=None):
+        import torch
+        gdt = torch.float32 if self.mode == MODE_F32_KAHAN else torch.float64
+        grad_out = grad_out.to(gdt).contiguous()
+        S = int(grad_out.shape[-1])
+        if grad_dens is None:
+            grad_dens = torch.zeros((self.tree.n_leaves, S), dtype=torch.float64, device=grad_out.device)
+        _check(_lib.rt_paths_adjoint(self._h, _dptr(grad_out), S, _dptr(grad_dens), _stream(stream)))
+        return grad_dens
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.rt_destroy_paths(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def trace_columns_adjoint(tree: Octree, src, nside: int, grad_out, mode="f32k", grad_dens=None,
-                          stream=None):
+                          stream=None, path_policy: int = 1):
     """grad_dens[j,k] += sum over rays of grad_out[s,q,k] * ds(s,q,j) (float64)."""
     import torch
     m = _mode(mode)
@@ -225,7 +284,8 @@ def trace_columns_adjoint(tree: Octree, src, nside: int, grad_out, mode="f32k", 
     if grad_dens is None:
         grad_dens = torch.zeros((tree.n_leaves, S), dtype=torch.float64, device=src.device)
     _check(_lib.rt_trace_columns_adjoint(tree.handle, _dptr(src), int(src.shape[0]), int(nside),
-                                         _dptr(grad_out), S, m, _dptr(grad_dens), 1, _stream(stream)))
+                                         _dptr(grad_out), S, m, _dptr(grad_dens), int(path_policy),
+                                         _stream(stream)))
     return grad_dens
 
 

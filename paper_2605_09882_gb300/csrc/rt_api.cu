@@ -163,6 +163,7 @@ static int prepare(const rt_octree* t, const double* d_src, int64_t n_src, int n
     a.S = S;
     a.st = t->st;
     a.batch = g_batch;
+    a.layout = ray_layout(n_src);
     return RT_OK;
 }
 
@@ -279,12 +280,20 @@ int rt_trace_columns_adjoint(const rt_octree* t, const double* d_src, int64_t n_
     TraceArgs a;
     int st = prepare(t, d_src, n_src, nside, n_species, mode, a, "rt_trace_columns_adjoint");
     if (st != RT_OK) return st;
-    if (path_policy != 0 && path_policy != 1)
-        return set_error(RT_ERR_ARG, "rt_trace_columns_adjoint: only path_policy 0 (auto) and 1 (recompute) exist");
+    if (path_policy < 0 || path_policy > 2)
+        return set_error(RT_ERR_ARG, "rt_trace_columns_adjoint: path_policy must be 0, 1 or 2");
     if (n_src == 0) return RT_OK;
     if (!d_grad_out || !d_grad_dens) return set_error(RT_ERR_ARG, "rt_trace_columns_adjoint: null gradient pointer");
     if (!aligned16(d_grad_out) || !aligned16(d_grad_dens))
         return set_error(RT_ERR_ARG, "rt_trace_columns_adjoint: gradients must be 16-byte aligned");
+    if (path_policy == 2) {
+        rt_paths* p = nullptr;
+        st = rt_record_paths(t, d_src, n_src, nside, mode, stream, &p);
+        if (st != RT_OK) return st;
+        st = rt_paths_adjoint(p, d_grad_out, n_species, d_grad_dens, stream);
+        rt_destroy_paths(p);
+        return st;
+    }
     a.gin = d_grad_out;
     a.out = d_grad_dens;
     cudaStream_t s = (cudaStream_t)stream;

@@ -435,7 +435,12 @@ __device__ __forceinline__ int source_fixed(const double* __restrict__ src, cons
 // The leaf index is the level-L Morton index, kept per axis in dilated form;
 // the per-axis far-face distance A (an exact float) and the double-float exit
 // time change only on the axes that step.
-template <int VM, bool QZ, class V>
+//
+// LOCK (VM 3 or 7, QZ sources, bitwise-equal |inv_x| = |inv_y| and equal |A_x|,
+// |A_y| at the source): x and y keep equal |A| and equal exit times for the
+// whole walk (both grow by the leaf size whenever they step, together), so
+// their exits always tie exactly and the choice is {x, y} against {z}.
+template <int VM, bool QZ, bool LOCK, class V>
 __device__ __forceinline__ int walk_f32k_grid(const DevTree& t, const DirConst* __restrict__ dp,
                                               const double* __restrict__ src, long long cap, V& vis,
                                               WalkCounters& wc)
@@ -467,11 +472,29 @@ __device__ __forceinline__ int walk_f32k_grid(const DevTree& t, const DirConst* 
     }
     uint32_t j = dl[0] | dl[1] | dl[2];
     float tih = 0.f, til = 0.f;
-    for (long long step = 0;; ++step) {
-        if (step >= cap) return RT_ERR_STEP_LIMIT;
+    const int icap = (int)min(cap, (long long)0x7fffffff);
+    for (int step = 0;; ++step) {
+        if (step >= icap) return RT_ERR_STEP_LIMIT;
         vis.pre(j);
         int bs;
-        const unsigned E = exit_set<VM, QZ>(th, Af, qf, ih, flags, cE, dp, bs, wc);
+        unsigned E;
+        if (LOCK) {
+            if (VM == 3) {
+                E = 3u;
+                bs = 0;
+            } else if (__fsub_rn(th[2], th[0]) > (fabsf(th[2]) + fabsf(th[0])) * kER + 2.f * cE) {
+                E = 3u;
+                bs = 0;
+            } else if (__fsub_rn(th[0], th[2]) > (fabsf(th[2]) + fabsf(th[0])) * kER + 2.f * cE) {
+                E = 4u;
+                bs = 2;
+            } else {
+                E = resolve_exit<VM>(th, Af, qf, ih, flags, dp, th[2] < th[0] ? 2 : 0, wc);
+                bs = __ffs(E) - 1;
+            }
+        } else {
+            E = exit_set<VM, QZ>(th, Af, qf, ih, flags, cE, dp, bs, wc);
+        }
         const float ths = sel3(th, bs), tls = sel3(tl, bs);
         const float ds = __fmul_rn(__fadd_rn(__fsub_rn(ths, tih), __fsub_rn(tls, til)), 0x1p-21f);
         tih = ths;
@@ -486,7 +509,12 @@ __device__ __forceinline__ int walk_f32k_grid(const DevTree& t, const DirConst* 
                 if (c[b] == (pos ? N1 : 0)) leaving = true;
                 c[b] += pos ? 1 : -1;
                 Af[b] = __fadd_rn(Af[b], pos ? (float)size : -(float)size);
-                exit_time<QZ>(Af[b], ph[b], pl[b], ih[b], il[b], th[b], tl[b]);
+                if (LOCK && b == 1) {
+                    th[1] = th[0];  // equal |A| and |inv|: the same exit time
+                    tl[1] = tl[0];
+                } else {
+                    exit_time<QZ>(Af[b], ph[b], pl[b], ih[b], il[b], th[b], tl[b]);
+                }
                 const uint32_t mb = kDilX << b;
                 dl[b] = pos ? (((dl[b] | ~mb) + (1u << b)) & mb) : ((dl[b] - (1u << b)) & mb);
             }
@@ -497,7 +525,30 @@ __device__ __forceinline__ int walk_f32k_grid(const DevTree& t, const DirConst* 
     return RT_OK;
 }
 
+// True when the x and y exits of a QZ source on a uniform grid stay locked:
+// both axes move, |inv_x| = |inv_y| bitwise, and the source is as far from
+// its leaf's far x face as from its far y face.
+__device__ __forceinline__ bool xy_locked(const DevTree& t, int flags, const double* __restrict__ src)
+{
+    if ((flags & 3) != 3 || !inv_equal(flags, 0, 1)) return false;
+    long long qx, qy;
+    if (!fixed_source(src[0], qx) || !fixed_source(src[1], qy)) return false;
+    const int sh = kDepth - t.uniform_level;
+    const int size = 1 << sh;
+    const int rx = (int)(qx >> 32) & (size - 1), ry = (int)(qy >> 32) & (size - 1);
+    const int ax = ((flags >> 3) & 1) ? size - rx : rx;
+    const int ay = ((flags >> 4) & 1) ? size - ry : ry;
+    return ax == ay;
+}
+
 // ------------------------------------ F32-Kahan walk on a general octree
+
+// floor(v) for |v| < 2^22 without a conversion instruction: v + 1.5 * 2^23
+// rounded down lies in [2^23, 2^24), where floats are the integers.
+__device__ __forceinline__ int floor_small(float v)
+{
+    return __float_as_int(__fadd_rd(v, 12582912.0f)) - 0x4B400000;
+}
 
 // Exact float of an integer 0 <= v < 2^23 without a conversion instruction.
 __device__ __forceinline__ float small_int_to_float(uint32_t v)
@@ -625,10 +676,11 @@ __device__ __forceinline__ int walk_f32k_tree(const DevTree& t, const DirConst* 
                 const float w = QZ ? mw : __fadd_rn(mw, ph[b]);
                 const float del = (fabsf(mw) + fabsf(w)) * 0x1p-21f + fabsf(m32[b]) * fabsf(ihe) * 0x1p-22f +
                                   0x1p-22f;
-                const long long l0 = (long long)qi[b] + (long long)floorf(__fsub_rd(w, del));
-                const long long l1 = (long long)qi[b] + (long long)floorf(__fadd_ru(w, del));
-                c[b] = (uint32_t)min(max(l0, (long long)lo[b]), (long long)hib);
-                chi[b] = (uint32_t)min(max(l1, (long long)lo[b]), (long long)hib);
+                // |w| + del < 2^22: floor by adding 1.5 * 2^23 rounded down
+                const int l0 = qi[b] + floor_small(__fsub_rd(w, del));
+                const int l1 = qi[b] + floor_small(__fadd_ru(w, del));
+                c[b] = (uint32_t)min(max(l0, (int)lo[b]), (int)hib);
+                chi[b] = (uint32_t)min(max(l1, (int)lo[b]), (int)hib);
                 wide |= chi[b] != c[b];
             }
         }
@@ -686,14 +738,18 @@ __device__ __forceinline__ int walk_grid_vm(int vm, const DevTree& t, const DirC
                                             const double* __restrict__ src, long long cap, V& vis,
                                             WalkCounters& wc)
 {
+    if (QZ && (vm == 3 || vm == 7) && xy_locked(t, __ldg(&dp->flags), src)) {
+        if (vm == 3) return walk_f32k_grid<3, true, true>(t, dp, src, cap, vis, wc);
+        return walk_f32k_grid<7, true, true>(t, dp, src, cap, vis, wc);
+    }
     switch (vm) {
-    case 1: return walk_f32k_grid<1, QZ>(t, dp, src, cap, vis, wc);
-    case 2: return walk_f32k_grid<2, QZ>(t, dp, src, cap, vis, wc);
-    case 3: return walk_f32k_grid<3, QZ>(t, dp, src, cap, vis, wc);
-    case 4: return walk_f32k_grid<4, QZ>(t, dp, src, cap, vis, wc);
-    case 5: return walk_f32k_grid<5, QZ>(t, dp, src, cap, vis, wc);
-    case 6: return walk_f32k_grid<6, QZ>(t, dp, src, cap, vis, wc);
-    default: return walk_f32k_grid<7, QZ>(t, dp, src, cap, vis, wc);
+    case 1: return walk_f32k_grid<1, QZ, false>(t, dp, src, cap, vis, wc);
+    case 2: return walk_f32k_grid<2, QZ, false>(t, dp, src, cap, vis, wc);
+    case 3: return walk_f32k_grid<3, QZ, false>(t, dp, src, cap, vis, wc);
+    case 4: return walk_f32k_grid<4, QZ, false>(t, dp, src, cap, vis, wc);
+    case 5: return walk_f32k_grid<5, QZ, false>(t, dp, src, cap, vis, wc);
+    case 6: return walk_f32k_grid<6, QZ, false>(t, dp, src, cap, vis, wc);
+    default: return walk_f32k_grid<7, QZ, false>(t, dp, src, cap, vis, wc);
     }
 }
 

@@ -67,7 +67,18 @@ struct TraceArgs {
     uint64_t* hash;
     DevStats* st;
     int batch;               // 32-ray groups per queue pop
+    int layout;              // ray order: 0 direction-major (sources padded to 32), 1 source-major
+    // path recording (KIND 3): per 32-ray group, segment k of lane i is entry
+    // rec_off[g] + 32 k + i of rec_leaf / rec_ds
+    const long long* rec_off;
+    uint32_t* rec_leaf;
+    void* rec_ds;
 };
+
+// Ray order of a trace: direction-major (32 neighbouring sources share a
+// direction in a warp) unless there are too few sources to fill a warp, then
+// source-major (a warp walks 32 directions of the same source).
+inline int ray_layout(int64_t n_src) { return n_src < 32 ? 1 : 0; }
 
 // Launch helpers (defined in the .cu files).
 cudaError_t launch_forward(const TraceArgs& a, int mode, int block, int grid, cudaStream_t s);

@@ -10,12 +10,13 @@
 
 // Resident 256-thread blocks per SM the register budget is sized for: the
 // uniform-grid F32-Kahan walk runs best at 64 registers (4 blocks), the
-// others keep the compiler's choice.
+// general-octree one at 85 (3 blocks); the FP64 walks keep the compiler's
+// choice.
 #ifndef RT_MIN_BLOCKS_GRID
 #define RT_MIN_BLOCKS_GRID 4
 #endif
 #ifndef RT_MIN_BLOCKS_TREE
-#define RT_MIN_BLOCKS_TREE 1
+#define RT_MIN_BLOCKS_TREE 3
 #endif
 #ifndef RT_MIN_BLOCKS
 #define RT_MIN_BLOCKS 1
@@ -108,6 +109,25 @@ struct AdjScatter {  // grad[j,k] += g[k] * ds
     __device__ __forceinline__ void seg(uint32_t j, F ds) { pre(j); acc(ds); }
 };
 
+template <class T>
+struct PathRecord {  // (leaf, ds) of segment k at base + 32 k, never at or past lim
+    uint32_t* leaf;
+    T* ds;
+    long long pos, lim;
+    __device__ __forceinline__ void pre(uint32_t j)
+    {
+        if (pos < lim) leaf[pos] = j;
+    }
+    template <class F>
+    __device__ __forceinline__ void acc(F d)
+    {
+        if (pos < lim) ds[pos] = (T)d;
+        pos += 32;
+    }
+    template <class F>
+    __device__ __forceinline__ void seg(uint32_t j, F d) { pre(j); acc(d); }
+};
+
 // ------------------------------------------------------------ common loop
 
 __device__ __forceinline__ void flush_counters(DevStats* st, unsigned long long rays,
@@ -129,14 +149,15 @@ __device__ __forceinline__ void flush_counters(DevStats* st, unsigned long long 
     }
 }
 
-// KIND 0: forward columns; 1: path fingerprints; 2: adjoint scatter.
+// KIND 0: forward columns; 1: path fingerprints; 2: adjoint scatter;
+// 3: path recording.
 template <int KIND, int MODE, bool UNIFORM, int SM>
 __global__ void __launch_bounds__(256, (MODE == RT_MODE_F32_KAHAN) ? (UNIFORM ? RT_MIN_BLOCKS_GRID : RT_MIN_BLOCKS_TREE)
                                                                 : RT_MIN_BLOCKS)
 k_trace(const TraceArgs a)
 {
     const int lane = threadIdx.x & 31;
-    const unsigned long long total = (unsigned long long)a.n_src_pad * (unsigned long long)a.nd;
+    const unsigned long long total = (unsigned long long)(a.layout ? a.n_src : a.n_src_pad) * (unsigned long long)a.nd;
     const long long cap = a.t.step_cap;
     unsigned long long n_rays = 0, n_segs = 0, n_efb = 0, n_lfb = 0;
     for (;;) {
@@ -147,9 +168,18 @@ k_trace(const TraceArgs a)
         for (int kk = 0; kk < a.batch; kk++) {
             const unsigned long long g0 = base + 32ull * kk;
             if (g0 >= total) break;
-            const int q = (int)(g0 / (unsigned long long)a.n_src_pad);
-            const long long s = (long long)(g0 - (unsigned long long)q * a.n_src_pad) + lane;
-            if (s >= a.n_src) continue;
+            int q;
+            long long s;
+            if (a.layout == 0) {
+                q = (int)(g0 / (unsigned long long)a.n_src_pad);
+                s = (long long)(g0 - (unsigned long long)q * a.n_src_pad) + lane;
+                if (s >= a.n_src) continue;
+            } else {
+                const unsigned long long r = g0 + lane;
+                if (r >= total) continue;
+                s = (long long)(r / (unsigned long long)a.nd);
+                q = (int)(r - (unsigned long long)s * a.nd);
+            }
             const DirConst* d = a.dirs + q;
             const long long ray = s * a.nd + q;
             const double* src = a.src + 3 * s;
@@ -187,6 +217,17 @@ k_trace(const TraceArgs a)
                 if (st != RT_OK) { report_fault(a.st, st, ray); v.h = 0; wc.nseg = 0; }
                 if (a.nseg) a.nseg[ray] = wc.nseg;
                 if (a.hash) a.hash[ray] = v.h;
+            } else if (KIND == 3) {
+                const long long pos = a.rec_off[g0 >> 5] + lane, lim = a.rec_off[(g0 >> 5) + 1];
+                if (MODE == RT_MODE_FP64) {
+                    PathRecord<double> v = {a.rec_leaf, (double*)a.rec_ds, pos, lim};
+                    const int st = walk<MODE, UNIFORM>(a.t, d, src, cap, v, wc);
+                    if (st != RT_OK) report_fault(a.st, st, ray);
+                } else {
+                    PathRecord<float> v = {a.rec_leaf, (float*)a.rec_ds, pos, lim};
+                    const int st = walk<MODE, UNIFORM>(a.t, d, src, cap, v, wc);
+                    if (st != RT_OK) report_fault(a.st, st, ray);
+                }
             } else {
                 AdjScatter<SM> v;
                 v.grad = (double*)a.out;

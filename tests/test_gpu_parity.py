@@ -217,3 +217,17 @@ def test_bad_arguments_are_rejected(rt):
     out = rt.trace_columns(tree, src[:0], 1, dens[:, :1], "f32k")
     assert out.shape == (0, 12, 1)
     tree.close()
+
+
+def test_few_sources_many_directions(rt):
+    """Angular-convergence shape: a handful of sources at high Nside (the
+    source-major ray order, a warp walks 32 directions of one source)."""
+    rng = np.random.default_rng(91)
+    keys, lev, _ = random_octree(rng, 2, 7, 0.3)
+    dens = rng.uniform(0.1, 10.0, size=(keys.shape[0], 1))
+    src = np.array([[0.5, 0.5, 0.5], [0.3125, 0.7, 0.41], [0.1, 0.9, 0.5]])
+    for nside in (8, 16):
+        _check_case(rt, keys, lev, dens, src, nside, label=f"few nside{nside}")
+    cloud = synth.uniform_cloud(5, 1.0, 4, fracs=(1.0,), dtype=np.float64)
+    _check_case(rt, cloud.keys, cloud.levels, cloud.dens, np.array([[0.515625, 0.515625, 0.515625]]), 16,
+                label="uniform centre nside16")
