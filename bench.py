@@ -42,7 +42,7 @@ def parse():
     p.add_argument("--no-extras", action="store_true", help="skip FP64 form, adjoint, e2e, CPU baseline")
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
     p.add_argument("--workload", default="uniform512",
-                   choices=["uniform512", "amr128", "batched64", "adjoint_amr64"],
+                   choices=["uniform512", "amr128", "batched64", "adjoint_amr64", "dualgrid256"],
                    help="uniform512 is the benchmark; the others run one secondary workload alone")
     return p.parse_args()
 
@@ -273,6 +273,36 @@ def adjoint_leg(rt, dev, stream, reps=3):
             "adjoint_over_forward": ta / tf}
 
 
+def dualgrid_leg(rt, dev, stream, level=8, reps=1):
+    """The paper's dual grid: a uniform source grid (2^level cells per axis,
+    lognormal sigma 2, 4 species); the contribution grid is built from it on
+    the GPU (split while n_max >= 1 and (n_max - n_min) / n_max >= 1 %); rays
+    leave every source-cell centre (Nside 1) through that AMR grid."""
+    import torch
+    from synth import torchgen
+    keys_u, lev_u, dens_u, ntot = torchgen.uniform_cloud(level, 2.0, 6, device=dev)
+    tb0 = torch.cuda.Event(enable_timing=True)
+    tb1 = torch.cuda.Event(enable_timing=True)
+    tb0.record(stream)
+    keys, lev, dens = rt.build_amr(ntot, dens_u, 1.0, 0.01, level)
+    tb1.record(stream)
+    torch.cuda.synchronize()
+    tree = rt.Octree(keys, lev)
+    src = torchgen.uniform_centres(level, torch.arange(keys_u.numel(), device=dev))
+    out = torch.empty((src.shape[0], 12, 4), dtype=torch.float32, device=dev)
+    tree.reset_stats()
+    t = timed(lambda: rt.trace_columns(tree, src, 1, dens, "f32k", out=out), stream, reps=reps)
+    st = tree.stats()
+    assert st["status"] == 0, st
+    segs = st["segments"] / (reps + 1)
+    res = {"workload": "dual grid: %d^3 source cells, contribution grid of %d leaves built from them "
+                       "(n_PDR 1, 1%% variation), Nside 1" % (1 << level, keys.numel()),
+           "value": segs / t, "unit": "ray-segments/s", "ms_per_step": t * 1e3, "segments_per_step": int(segs),
+           "build_amr_ms": tb0.elapsed_time(tb1)}
+    tree.close()
+    return res
+
+
 # -------------------------------------------------------------- reference
 
 def run_reference(a, rank, world):
@@ -339,6 +369,8 @@ def main():
         elif a.workload == "batched64":
             r = batched_leg(rt, dev, stream, os.path.join(ROOT, "paper_2605_09882_gb300", "autotune_gb300.json"),
                             reps=a.steps)
+        elif a.workload == "dualgrid256":
+            r = dualgrid_leg(rt, dev, stream, reps=a.steps)
         else:
             r = adjoint_leg(rt, dev, stream, reps=a.steps)
         if rank == 0:
@@ -435,6 +467,17 @@ def main():
         extras["adjoint"] = {"ms_per_step": tadj * 1e3, "adjoint_over_forward": tadj / avg_launch_s}
         del grad
         torch.cuda.empty_cache()
+        # ---- fused A_V,eff epilogue: N_H = n(H) + 2 n(H2), a = A_V0 x 125 pc
+        AV0_CM2, BOX_CM = 6.29e-22, 125 * 3.0857e18
+        av = torch.empty(n, dtype=torch.float64, device=dev)
+        tree.reset_stats()
+        tav = timed(lambda: rt.trace_epilogue(tree, src, NSIDE, dens, "av_eff", [1.0, 2.0], AV0_CM2 * BOX_CM,
+                                              gamma=3.02, out=av), stream)
+        sav = tree.stats()
+        extras["av_eff_epilogue"] = {"value": sav["segments"] / 2 / tav, "unit": "ray-segments/s",
+                                     "ms_per_step": tav * 1e3, "output_bytes": n * 8,
+                                     "what": "A_V,eff per source (N_H = n_H + 2 n_H2, gamma 3.02, 125 pc box) "
+                                             "computed inside the trace; no column write"}
         # ---- octree build (validation + coarse table), one-time per tree
         tb = timed(lambda: rt.Octree(keys, lev).close(), stream)
         extras["build_octree_ms"] = tb * 1e3
@@ -456,6 +499,10 @@ def main():
                    "kind": "oracle",
                    "sample": f"{r['n_src']} random leaf-centre sources x 12 rays ({r['segments']} segments), "
                              f"CPU {cpu_model()}"}
+            from oracle import epilogue as oep
+            want_av = oep.av_eff(r["cols"], [1.0, 2.0, 0.0, 0.0], AV0_CM2 * BOX_CM, 3.02)
+            got_av = av[torch.from_numpy(r["idx"]).to(dev)].cpu().numpy()
+            extras["av_eff_epilogue"]["parity_max_rel"] = float(np.max(np.abs(got_av - want_av) / np.abs(want_av)))
             extras["parity_sample"] = {"n_src": r["n_src"], "max_rel": float(err.max()),
                                        "max_rel_per_species": [float(x) for x in err.max(axis=(0, 1))],
                                        "mean_rel_per_species": [float(x) for x in err.mean(axis=(0, 1))]}

@@ -124,6 +124,38 @@ int rt_trace_columns(const rt_octree* tree, const double* d_src, int64_t n_src, 
                      const void* d_dens, int n_species, int dens_dtype, int mode,
                      void* d_out, void* stream);
 
+/* Per-source quantities computed inside the trace, so that the columns are
+ * never written (the paper's 3D-PDR coupling, Sec. 2.4, and its accuracy
+ * test, Sec. 3).  Each ray's combined column is N = sum_k weights[k] I_k, a
+ * linear combination of its species columns (as in the optical depth's
+ * [n_j g_i / g_j - n_i] integrand).
+ *   RT_EPI_AV_EFF:      out[p] = -(1/gamma) ln( (1/N_rays) sum_q exp(-gamma a N_pq) )
+ *                       (A_V,eff; a = A_V0 x box length in the columns' unit)
+ *   RT_EPI_BETA:        out[p] = (1/N_rays) sum_q (1 - exp(-tau_pq)) / tau_pq,
+ *                       tau_pq = c_p N_pq, c_p = d_coef[p] (or a if d_coef is NULL);
+ *                       a term is 1 at tau = 0 (escape probability)
+ *   RT_EPI_ATTENUATION: out[p][q] = exp(-a N_pq) (attenuation I / I_0)
+ * The FP64 arithmetic of the epilogue uses the CUDA math library's exp and
+ * expm1. */
+enum rt_epilogue_kind { RT_EPI_AV_EFF = 1, RT_EPI_BETA = 2, RT_EPI_ATTENUATION = 3 };
+
+typedef struct rt_epilogue {
+    int kind;                 /* rt_epilogue_kind */
+    int reserved;
+    double weights[8];        /* species weights; entries past n_species ignored */
+    double a;                 /* extinction / opacity per unit combined column */
+    double gamma;             /* A_V,eff only (3.02 in the paper) */
+    const double* d_coef;     /* beta only: per-source c_p [n_src] or NULL */
+} rt_epilogue;
+
+/* Traces like rt_trace_columns and writes only the epilogue:
+ *   d_out: float64 [n_src] (A_V,eff, beta) or [n_src][12 nside^2]
+ *   (attenuation).  Per-source sums use FP64 atomics across the directions,
+ *   so their order is not fixed. */
+int rt_trace_epilogue(const rt_octree* tree, const double* d_src, int64_t n_src, int nside,
+                      const void* d_dens, int n_species, int dens_dtype, int mode,
+                      const rt_epilogue* h_epi, double* d_out, void* stream);
+
 /* Per-ray path fingerprints: the number of segments and the hash
  * h <- (h XOR leaf) * 0x100000001b3 (h0 = 0xcbf29ce484222325) over the
  * visited leaf indices in walk order, for every ray of the walk that
@@ -147,6 +179,28 @@ int rt_trace_paths(const rt_octree* tree, const double* d_src, int64_t n_src, in
 int rt_trace_columns_adjoint(const rt_octree* tree, const double* d_src, int64_t n_src,
                              int nside, const void* d_grad_out, int n_species, int mode,
                              double* d_grad_dens, int path_policy, void* stream);
+
+/* Builds the contribution grid from a uniform source grid (Sec. 2.2.1:
+ * cells split recursively into eight children down to a maximum depth;
+ * Sec. 2.4: a cell splits only if n_max >= n_pdr and
+ * (n_max - n_min) / n_max >= rel_var, evaluated in FP64 exactly as written).
+ * A leaf's value is the mean of the source cells it covers.
+ *   d_nref: [8^level] refinement density (nref_dtype), the source grid of
+ *     2^level cells per axis in Morton order (cell i = interleave(x, y, z)
+ *     at that level); level 1..10.
+ *   d_vals: [8^level][n_species] values averaged into the leaves (vals_dtype,
+ *     Morton order), or NULL to average d_nref itself (n_species = 1).
+ *   max_level: deepest leaf level (<= level; also the minimum cell size).
+ *   d_keys, d_levels, d_leaf_vals ([capacity][n_species] of vals_dtype):
+ *     outputs, caller-allocated with capacity >= 8^level; the leaves come out
+ *     sorted by key, ready for rt_build_octree.
+ *   h_n_leaves: receives the number of leaves (the call synchronizes).
+ * Allocates and frees its own scratch (about 1.2 x 8^(level-1) cells of
+ * pyramid). */
+int rt_build_amr(const void* d_nref, int nref_dtype, const void* d_vals, int n_species, int vals_dtype,
+                 int level, double n_pdr, double rel_var, int max_level, uint64_t* d_keys,
+                 uint8_t* d_levels, void* d_leaf_vals, int64_t capacity, int64_t* h_n_leaves,
+                 void* stream);
 
 /* ---------------------------------------------------------- recorded paths
  * The (leaf, ds) sequence of every ray, recorded once so that the forward

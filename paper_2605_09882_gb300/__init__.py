@@ -14,7 +14,7 @@ import numpy as np
 
 from . import _build
 
-__all__ = ["Octree", "Batch", "Paths", "healpix_dirs", "trace_columns", "trace_paths", "trace_columns_adjoint",
+__all__ = ["Octree", "Batch", "Paths", "trace_epilogue", "build_amr", "healpix_dirs", "trace_columns", "trace_paths", "trace_columns_adjoint",
            "Columns", "RTError", "MODE_FP64", "MODE_F32_KAHAN", "set_launch", "lib_path"]
 
 MODE_FP64, MODE_F32_KAHAN = 0, 1
@@ -34,6 +34,14 @@ class CloudDesc(C.Structure):
     _fields_ = [("tree", C.c_void_p), ("d_src", C.c_void_p), ("n_src", C.c_int64), ("nside", C.c_int),
                 ("n_species", C.c_int), ("d_dens", C.c_void_p), ("dens_dtype", C.c_int),
                 ("reserved", C.c_int), ("d_out", C.c_void_p)]
+
+
+class Epilogue(C.Structure):
+    _fields_ = [("kind", C.c_int), ("reserved", C.c_int), ("weights", C.c_double * 8), ("a", C.c_double),
+                ("gamma", C.c_double), ("d_coef", C.c_void_p)]
+
+
+EPI_AV_EFF, EPI_BETA, EPI_ATTENUATION = 1, 2, 3
 
 
 class Stats(C.Structure):
@@ -74,6 +82,9 @@ def _load():
     lib.rt_batch_destroy.argtypes = [P]
     lib.rt_batch_destroy.restype = None
     lib.rt_autotune.argtypes = [P, C.c_char_p, C.POINTER(C.c_int * 3), C.POINTER(C.c_double), P]
+    lib.rt_trace_epilogue.argtypes = [P, P, i64, i32, P, i32, i32, i32, C.POINTER(Epilogue), P, P]
+    lib.rt_build_amr.argtypes = [P, i32, P, i32, i32, i32, C.c_double, C.c_double, i32, P, P, P, i64,
+                                 C.POINTER(i64), P]
     lib.rt_record_paths.argtypes = [P, P, i64, i32, i32, P, C.POINTER(P)]
     lib.rt_paths_info.argtypes = [P, C.POINTER(i64), C.POINTER(i64), C.POINTER(i64)]
     lib.rt_paths_columns.argtypes = [P, P, i32, i32, P, P]
@@ -217,6 +228,60 @@ def trace_paths(tree: Octree, src, nside: int, mode="f32k", stream=None):
     _check(_lib.rt_trace_paths(tree.handle, _dptr(src), int(src.shape[0]), int(nside), m,
                                _dptr(nseg), _dptr(hsh), _stream(stream)))
     return nseg, hsh
+
+
+def trace_epilogue(tree: Octree, src, nside: int, dens, kind, weights, a, gamma=3.02, coef=None, mode="f32k",
+                   out=None, stream=None):
+    """Per-source A_V,eff / escape probability (float64 [n_src]) or per-ray
+    attenuation (float64 [n_src][12 nside^2]) computed inside the trace; the
+    columns are never written.  kind: "av_eff", "beta" or "attenuation"."""
+    import torch
+    k = {"av_eff": EPI_AV_EFF, "beta": EPI_BETA, "attenuation": EPI_ATTENUATION}.get(kind, kind)
+    m = _mode(mode)
+    src = _check_src(src)
+    dens = dens.contiguous()
+    if dens.dim() == 1:
+        dens = dens[:, None]
+    S = int(dens.shape[1])
+    w = list(weights) + [0.0] * (8 - len(weights))
+    e = Epilogue(k, 0, (C.c_double * 8)(*w), float(a), float(gamma), _dptr(coef) if coef is not None else None)
+    shape = (src.shape[0], 12 * nside * nside) if k == EPI_ATTENUATION else (src.shape[0],)
+    if out is None:
+        out = torch.empty(shape, dtype=torch.float64, device=src.device)
+    _check(_lib.rt_trace_epilogue(tree.handle, _dptr(src), int(src.shape[0]), int(nside), _dptr(dens), S,
+                                  F64 if dens.dtype == torch.float64 else F32, m, C.byref(e), _dptr(out),
+                                  _stream(stream)))
+    return out
+
+
+def build_amr(nref, vals=None, n_pdr=1.0, rel_var=0.01, max_level=None, stream=None):
+    """Contribution grid from a uniform source grid in Morton order (8^L
+    cells): the split criterion n_max >= n_pdr and (n_max - n_min) / n_max >=
+    rel_var, recursively to max_level.  Returns keys (int64), levels (uint8)
+    and leaf means ([n_leaves][S], the dtype of vals)."""
+    import torch
+    n = int(nref.numel())
+    L = n.bit_length() - 1
+    if n != 1 << L or L % 3:
+        raise ValueError("nref must hold 8^level cells")
+    L //= 3
+    nref = nref.contiguous()
+    if vals is not None:
+        vals = vals.contiguous()
+        if vals.dim() == 1:
+            vals = vals[:, None]
+    S = 1 if vals is None else int(vals.shape[1])
+    vdt = (vals if vals is not None else nref).dtype
+    keys = torch.empty(n, dtype=torch.int64, device=nref.device)
+    lev = torch.empty(n, dtype=torch.uint8, device=nref.device)
+    out = torch.empty((n, S), dtype=vdt, device=nref.device)
+    nl = C.c_int64()
+    _check(_lib.rt_build_amr(_dptr(nref), F64 if nref.dtype == torch.float64 else F32, _dptr(vals), S,
+                             F64 if vdt == torch.float64 else F32, L, float(n_pdr), float(rel_var),
+                             L if max_level is None else int(max_level), _dptr(keys), _dptr(lev), _dptr(out), n,
+                             C.byref(nl), _stream(stream)))
+    m = nl.value
+    return keys[:m], lev[:m], out[:m]
 
 
 class Paths:

@@ -126,7 +126,7 @@ int sm_count_of(int dev) { return sm_count(dev); }
 static bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 
 // Common argument handling of the trace entry points.
-static int prepare(const rt_octree* t, const double* d_src, int64_t n_src, int nside, int S,
+int prepare_trace(const rt_octree* t, const double* d_src, int64_t n_src, int nside, int S,
                    int mode, TraceArgs& a, const char* who)
 {
     char buf[256];
@@ -236,7 +236,7 @@ int rt_trace_columns(const rt_octree* t, const double* d_src, int64_t n_src, int
                      void* stream)
 {
     TraceArgs a;
-    int st = prepare(t, d_src, n_src, nside, n_species, mode, a, "rt_trace_columns");
+    int st = prepare_trace(t, d_src, n_src, nside, n_species, mode, a, "rt_trace_columns");
     if (st != RT_OK) return st;
     if (dens_dtype != RT_F32 && dens_dtype != RT_F64) return set_error(RT_ERR_ARG, "rt_trace_columns: bad dens_dtype");
     if (n_src == 0) return RT_OK;
@@ -259,7 +259,7 @@ int rt_trace_paths(const rt_octree* t, const double* d_src, int64_t n_src, int n
                    uint32_t* d_nseg, uint64_t* d_hash, void* stream)
 {
     TraceArgs a;
-    int st = prepare(t, d_src, n_src, nside, 1, mode, a, "rt_trace_paths");
+    int st = prepare_trace(t, d_src, n_src, nside, 1, mode, a, "rt_trace_paths");
     if (st != RT_OK) return st;
     if (n_src == 0) return RT_OK;
     a.nseg = d_nseg;
@@ -278,7 +278,7 @@ int rt_trace_columns_adjoint(const rt_octree* t, const double* d_src, int64_t n_
                              int path_policy, void* stream)
 {
     TraceArgs a;
-    int st = prepare(t, d_src, n_src, nside, n_species, mode, a, "rt_trace_columns_adjoint");
+    int st = prepare_trace(t, d_src, n_src, nside, n_species, mode, a, "rt_trace_columns_adjoint");
     if (st != RT_OK) return st;
     if (path_policy < 0 || path_policy > 2)
         return set_error(RT_ERR_ARG, "rt_trace_columns_adjoint: path_policy must be 0, 1 or 2");

@@ -73,6 +73,11 @@ struct TraceArgs {
     const long long* rec_off;
     uint32_t* rec_leaf;
     void* rec_ds;
+    // fused epilogue (KIND 4): combined column N = sum_k epi_w[k] I_k per ray
+    int epi_kind;
+    double epi_w[kMaxSpecies];
+    double epi_a, epi_gamma;
+    const double* epi_coef;
 };
 
 // Ray order of a trace: direction-major (32 neighbouring sources share a
@@ -84,6 +89,8 @@ inline int ray_layout(int64_t n_src) { return n_src < 32 ? 1 : 0; }
 cudaError_t launch_forward(const TraceArgs& a, int mode, int block, int grid, cudaStream_t s);
 cudaError_t launch_paths(const TraceArgs& a, int mode, int block, int grid, cudaStream_t s);
 cudaError_t launch_adjoint(const TraceArgs& a, int mode, int block, int grid, cudaStream_t s);
+cudaError_t launch_epilogue(const TraceArgs& a, int mode, int block, int grid, cudaStream_t s);
+int occupancy_epi(int mode, int S, bool uniform, int block);
 int occupancy_fwd(int kind, int mode, int S, bool uniform, int block);
 int occupancy_adj(int mode, int S, bool uniform, int block);
 

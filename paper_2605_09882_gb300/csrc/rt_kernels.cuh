@@ -150,7 +150,23 @@ __device__ __forceinline__ void flush_counters(DevStats* st, unsigned long long 
 }
 
 // KIND 0: forward columns; 1: path fingerprints; 2: adjoint scatter;
-// 3: path recording.
+// 3: path recording; 4: fused per-source epilogue of the columns.
+
+// The epilogue of one ray from its combined column N: exp(-gamma a N) summed
+// per source (A_V,eff), (1 - exp(-tau)) / tau with tau = coef N summed per
+// source (beta), or exp(-a N) stored per ray (attenuation).
+__device__ __forceinline__ void ray_epilogue(const TraceArgs& a, long long s, long long ray, double N)
+{
+    double* out = (double*)a.out;
+    if (a.epi_kind == RT_EPI_AV_EFF) {
+        atomicAdd(out + s, exp(-a.epi_gamma * a.epi_a * N));
+    } else if (a.epi_kind == RT_EPI_BETA) {
+        const double tau = (a.epi_coef ? __ldg(a.epi_coef + s) : a.epi_a) * N;
+        atomicAdd(out + s, tau == 0.0 ? 1.0 : -expm1(-tau) / tau);
+    } else {
+        out[ray] = exp(-a.epi_a * N);
+    }
+}
 template <int KIND, int MODE, bool UNIFORM, int SM>
 __global__ void __launch_bounds__(256, (MODE == RT_MODE_F32_KAHAN) ? (UNIFORM ? RT_MIN_BLOCKS_GRID : RT_MIN_BLOCKS_TREE)
                                                                 : RT_MIN_BLOCKS)
@@ -217,6 +233,28 @@ k_trace(const TraceArgs a)
                 if (st != RT_OK) { report_fault(a.st, st, ray); v.h = 0; wc.nseg = 0; }
                 if (a.nseg) a.nseg[ray] = wc.nseg;
                 if (a.hash) a.hash[ray] = v.h;
+            } else if (KIND == 4) {
+                double N = 0.0;
+                if (MODE == RT_MODE_FP64) {
+                    FwdF64<SM> v;
+                    v.dens = a.dens; v.f64 = a.dens_f64; v.S = a.S;
+                    v.init();
+                    const int st = walk<MODE, UNIFORM>(a.t, d, src, cap, v, wc);
+                    if (st != RT_OK) { report_fault(a.st, st, ray); v.init(); }
+#pragma unroll
+                    for (int k = 0; k < SM; k++)
+                        if (k < a.S) N = __dadd_rn(N, __dmul_rn(a.epi_w[k], v.col[k]));
+                } else {
+                    FwdKahan<SM> v;
+                    v.dens = a.dens; v.f64 = a.dens_f64; v.S = a.S;
+                    v.init();
+                    const int st = walk<MODE, UNIFORM>(a.t, d, src, cap, v, wc);
+                    if (st != RT_OK) { report_fault(a.st, st, ray); v.init(); }
+#pragma unroll
+                    for (int k = 0; k < SM; k++)
+                        if (k < a.S) N = __dadd_rn(N, __dmul_rn(a.epi_w[k], (double)v.sum[k]));
+                }
+                ray_epilogue(a, s, ray, N);
             } else if (KIND == 3) {
                 const long long pos = a.rec_off[g0 >> 5] + lane, lim = a.rec_off[(g0 >> 5) + 1];
                 if (MODE == RT_MODE_FP64) {
