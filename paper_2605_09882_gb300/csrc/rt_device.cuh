@@ -264,6 +264,72 @@ __device__ __forceinline__ int walk_fp64(const DevTree& t, const DirConst& d,
     return RT_OK;
 }
 
+// FP64 walk on a full cube of equal-level leaves, moving axes VM (compile
+// time): the same operations as walk_fp64 (t_b = (F_b - Q_b) * inv_b with the
+// exact face F_b, t_out = min, E = {t_b == t_out}, ds = t_out - t_in), but a
+// face and its exit time are recomputed only on the axes that step, and the
+// leaf index is the dilated Morton index.
+template <int VM, class V>
+__device__ __forceinline__ int walk_fp64_grid(const DevTree& t, const DirConst* __restrict__ dp,
+                                              const double* __restrict__ src, long long cap, V& vis,
+                                              WalkCounters& wc)
+{
+    const int sh = kDepth - t.uniform_level;
+    const int N1 = (1 << t.uniform_level) - 1;
+    const double hsz = (double)(1 << sh) * 0x1p-21;  // leaf size, exact
+    const int flags = __ldg(&dp->flags);
+    double Q[3], F[3], tb[3], inv[3];
+    int c[3];
+    uint32_t dl[3];
+#pragma unroll
+    for (int b = 0; b < 3; b++) {
+        long long q;
+        if (!fixed_source(src[b], q)) return RT_ERR_SOURCE_OUTSIDE;
+        Q[b] = __dmul_rn(__ll2double_rn(q), 0x1p-53);
+        const uint32_t cb = (uint32_t)(q >> 32);
+        if (cb >= t.ext[b]) return RT_ERR_SOURCE_OUTSIDE;
+        c[b] = (int)(cb >> sh);
+        dl[b] = spread10((uint32_t)c[b]) << b;
+        F[b] = tb[b] = inv[b] = 0.0;
+        if (VM & (1 << b)) {
+            inv[b] = __ldg(&dp->inv[b]);
+            const int pos = (flags >> (3 + b)) & 1;
+            F[b] = __dmul_rn(__uint2double_rn((uint32_t)(c[b] + pos) << sh), 0x1p-21);
+            tb[b] = __dmul_rn(__dsub_rn(F[b], Q[b]), inv[b]);
+        }
+    }
+    uint32_t j = dl[0] | dl[1] | dl[2];
+    double t_in = 0.0;
+    const int icap = (int)min(cap, (long long)0x7fffffff);
+    for (int step = 0;; ++step) {
+        if (step >= icap) return RT_ERR_STEP_LIMIT;
+        vis.pre(j);
+        double t_out = __longlong_as_double(0x7ff0000000000000ll);
+#pragma unroll
+        for (int b = 0; b < 3; b++)
+            if (VM & (1 << b)) t_out = fmin(t_out, tb[b]);
+        vis.acc(__dsub_rn(t_out, t_in));
+        wc.nseg++;
+        t_in = t_out;
+        bool leaving = false;
+#pragma unroll
+        for (int b = 0; b < 3; b++) {
+            if ((VM & (1 << b)) && tb[b] == t_out) {
+                const int pos = (flags >> (3 + b)) & 1;
+                if (c[b] == (pos ? N1 : 0)) leaving = true;
+                c[b] += pos ? 1 : -1;
+                F[b] = __dadd_rn(F[b], pos ? hsz : -hsz);
+                tb[b] = __dmul_rn(__dsub_rn(F[b], Q[b]), inv[b]);
+                const uint32_t mb = kDilX << b;
+                dl[b] = pos ? (((dl[b] | ~mb) + (1u << b)) & mb) : ((dl[b] - (1u << b)) & mb);
+            }
+        }
+        if (leaving) break;
+        j = dl[0] | dl[1] | dl[2];
+    }
+    return RT_OK;
+}
+
 // ================================================= F32-Kahan walk (MODE 1)
 
 // Error bound of the FP32 exit time tp = fl(fl(A - ph) * ih) against the FP64
@@ -456,6 +522,13 @@ __device__ __forceinline__ int walk_f32k_grid(const DevTree& t, const DirConst* 
     float cE = 0.f;
     const int st = source_fixed(src, t, qi, qf, ph, pl);
     if (st != RT_OK) return st;
+    if (QZ) {  // the fractions are zero: let the compiler drop them
+#pragma unroll
+        for (int b = 0; b < 3; b++) {
+            qf[b] = 0u;
+            ph[b] = pl[b] = 0.f;
+        }
+    }
 #pragma unroll
     for (int b = 0; b < 3; b++) {
         c[b] = qi[b] >> sh;
@@ -776,6 +849,17 @@ __device__ __forceinline__ int walk(const DevTree& t, const DirConst* __restrict
                                     WalkCounters& wc)
 {
     if (MODE == RT_MODE_FP64) {
+        if (UNIFORM) {
+            switch (__ldg(&dp->flags) & 7) {
+            case 1: return walk_fp64_grid<1>(t, dp, src, cap, vis, wc);
+            case 2: return walk_fp64_grid<2>(t, dp, src, cap, vis, wc);
+            case 3: return walk_fp64_grid<3>(t, dp, src, cap, vis, wc);
+            case 4: return walk_fp64_grid<4>(t, dp, src, cap, vis, wc);
+            case 5: return walk_fp64_grid<5>(t, dp, src, cap, vis, wc);
+            case 6: return walk_fp64_grid<6>(t, dp, src, cap, vis, wc);
+            default: return walk_fp64_grid<7>(t, dp, src, cap, vis, wc);
+            }
+        }
         const DirConst d = *dp;
         return walk_fp64<UNIFORM>(t, d, src, cap, vis, wc);
     }
