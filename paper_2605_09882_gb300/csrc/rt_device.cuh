@@ -58,6 +58,9 @@ __device__ __forceinline__ uint32_t spread10(uint32_t v)
 
 constexpr uint32_t kDilX = 0x09249249u;  // bits 3b of a 30-bit Morton index
 
+// The bits of a 30-bit Morton index that belong to the two axes other than b.
+__device__ __forceinline__ constexpr uint32_t dil_holes(int b) { return ~(kDilX << b) & 0x3fffffffu; }
+
 // ------------------------------------------------------------- utilities
 
 __device__ __forceinline__ float sel3(const float v[3], int b)
@@ -400,10 +403,22 @@ __device__ __forceinline__ void order_exits(const float th[3], float& t1, int& i
     }
 }
 
+// D of axis b from its far-face distance A: (A 2^32) - qf.  MIR marks the
+// mirrored frame of the uniform-grid walk, where a negative axis carries
+// A' = -A, so that D' = -D = (A' 2^32) + qf.
+template <bool MIR>
+__device__ __forceinline__ long long face_distance(float A, uint32_t qf, int flags, int b)
+{
+    const long long hi = (long long)small_float_to_int(A) << 32;
+    if (MIR && !((flags >> (3 + b)) & 1)) return hi + (long long)qf;
+    return hi - (long long)qf;
+}
+
 // Exit set when the two smallest FP32 times are within the certified margin:
 // axes that tie exactly (bitwise-equal |inv| and equal |D|) are recognised in
-// integers, anything else is decided by the FP64 times of the definition.
-template <int VM>
+// integers, anything else is decided by the FP64 times of the definition
+// (|D| 2^-53 |inv|, the same value for either sign convention).
+template <int VM, bool MIR>
 __device__ __forceinline__ unsigned resolve_exit(const float th[3], const float Af[3], const uint32_t qf[3],
                                                  const float ih[3], int flags,
                                                  const DirConst* __restrict__ dp, int bs, WalkCounters& wc)
@@ -411,14 +426,14 @@ __device__ __forceinline__ unsigned resolve_exit(const float th[3], const float 
     unsigned E = 1u << bs;
     bool amb = false;
     const float tmin = sel3(th, bs);
-    const long long Ds = ((long long)small_float_to_int(sel3(Af, bs)) << 32) - (long long)sel3(qf, bs);
+    const long long Ds = face_distance<MIR>(sel3(Af, bs), sel3(qf, bs), flags, bs);
     const float errs = fabsf(tmin) * kER + fabsf(sel3(ih, bs)) * kEA;
 #pragma unroll
     for (int b = 0; b < 3; b++) {
         if ((VM & (1 << b)) && b != bs) {
             const float errb = fabsf(th[b]) * kER + fabsf(ih[b]) * kEA;
             if (__fsub_rn(th[b], tmin) <= errs + errb) {
-                const long long Db = ((long long)small_float_to_int(Af[b]) << 32) - (long long)qf[b];
+                const long long Db = face_distance<MIR>(Af[b], qf[b], flags, b);
                 if (inv_equal(flags, b, bs) && llabs(Db) == llabs(Ds)) E |= 1u << b;
                 else amb = true;
             }
@@ -432,8 +447,9 @@ __device__ __forceinline__ unsigned resolve_exit(const float th[3], const float 
         for (int b = 0; b < 3; b++) {
             tb[b] = mn;
             if (VM & (1 << b)) {
-                const long long D = ((long long)small_float_to_int(Af[b]) << 32) - (long long)qf[b];
-                tb[b] = __dmul_rn(__dmul_rn(__ll2double_rn(D), 0x1p-53), __ldg(&dp->inv[b]));
+                const long long D = face_distance<MIR>(Af[b], qf[b], flags, b);
+                const double inv = __ldg(&dp->inv[b]);
+                tb[b] = __dmul_rn(__dmul_rn(__ll2double_rn(D), 0x1p-53), MIR ? fabs(inv) : inv);
             }
         }
 #pragma unroll
@@ -449,7 +465,7 @@ __device__ __forceinline__ unsigned resolve_exit(const float th[3], const float 
 // Exit set of one step: the smallest exit time decides unless the second is
 // within the certified margin; then an exact tie of two equal-|inv| axes of a
 // QZ source is recognised from equal |A|, and anything else is resolved.
-template <int VM, bool QZ>
+template <int VM, bool QZ, bool MIR>
 __device__ __forceinline__ unsigned exit_set(const float th[3], const float Af[3], const uint32_t qf[3],
                                              const float ih[3], int flags, float cE,
                                              const DirConst* __restrict__ dp, int& bs, WalkCounters& wc)
@@ -469,7 +485,7 @@ __device__ __forceinline__ unsigned exit_set(const float th[3], const float Af[3
             done = true;
         }
         if (!done) {
-            E = resolve_exit<VM>(th, Af, qf, ih, flags, dp, i1, wc);
+            E = resolve_exit<VM, MIR>(th, Af, qf, ih, flags, dp, i1, wc);
             bs = __ffs(E) - 1;
         }
     }
@@ -498,9 +514,17 @@ __device__ __forceinline__ int source_fixed(const double* __restrict__ src, cons
 
 // Walk of one ray through a full cube of equal-level leaves (level L <= 10),
 // F32-Kahan arithmetic, for a direction whose moving axes are the bits of VM.
-// The leaf index is the level-L Morton index, kept per axis in dilated form;
-// the per-axis far-face distance A (an exact float) and the double-float exit
-// time change only on the axes that step.
+//
+// The walk runs in a mirrored frame: a moving axis with m_b < 0 is reflected
+// (cell c -> N1 - c = c ^ N1, distance A -> -A, inv -> -inv), so every moving
+// axis advances by +1 cell and every exit time is |A - frac| |inv|, bitwise
+// the value of the unreflected form because rounding is sign-symmetric.  Per
+// axis the walk keeps the far-face distance A (an exact float) and the
+// double-float exit time, changed only when the axis steps, and the mirrored
+// cell index in dilated Morton form with the other axes' bit positions set to
+// one, so that a step is one add and one OR and the leaf index is the AND of
+// the three fields, reflected back by one XOR.  The ray leaves the cube when
+// an exit axis steps out of a leaf whose far face is the domain boundary.
 //
 // LOCK (VM 3 or 7, QZ sources, bitwise-equal |inv_x| = |inv_y| and equal |A_x|,
 // |A_y| at the source): x and y keep equal |A| and equal exit times for the
@@ -513,12 +537,13 @@ __device__ __forceinline__ int walk_f32k_grid(const DevTree& t, const DirConst* 
 {
     const int sh = kDepth - t.uniform_level;
     const int N1 = (1 << t.uniform_level) - 1;
-    const int size = 1 << sh;
+    const float fsize = (float)(1 << sh);
     const int flags = __ldg(&dp->flags);
     float ih[3], il[3], ph[3], pl[3];
-    int qi[3], c[3];
+    int qi[3];
     uint32_t qf[3], dl[3];
-    float Af[3], th[3], tl[3];
+    uint32_t xm = 0u;
+    float Af[3], Alim[3], th[3], tl[3];
     float cE = 0.f;
     const int st = source_fixed(src, t, qi, qf, ph, pl);
     if (st != RT_OK) return st;
@@ -531,23 +556,30 @@ __device__ __forceinline__ int walk_f32k_grid(const DevTree& t, const DirConst* 
     }
 #pragma unroll
     for (int b = 0; b < 3; b++) {
-        c[b] = qi[b] >> sh;
-        dl[b] = spread10((uint32_t)c[b]) << b;
-        Af[b] = th[b] = tl[b] = ih[b] = il[b] = 0.f;
+        const int c = qi[b] >> sh;
+        const bool neg = (VM & (1 << b)) && !((flags >> (3 + b)) & 1);
+        dl[b] = (spread10((uint32_t)(neg ? (c ^ N1) : c)) << b) | dil_holes(b);
+        if (neg) xm |= spread10((uint32_t)N1) << b;
+        Af[b] = Alim[b] = th[b] = tl[b] = ih[b] = il[b] = 0.f;
         if (VM & (1 << b)) {
-            ih[b] = __ldg(&dp->ih[b]);
-            il[b] = __ldg(&dp->il[b]);
-            const int pos = (flags >> (3 + b)) & 1;
-            Af[b] = __int2float_rn(((c[b] + pos) << sh) - qi[b]);
+            ih[b] = fabsf(__ldg(&dp->ih[b]));
+            il[b] = neg ? -__ldg(&dp->il[b]) : __ldg(&dp->il[b]);
+            if (neg) {
+                ph[b] = -ph[b];
+                pl[b] = -pl[b];
+            }
+            Af[b] = __int2float_rn(neg ? qi[b] - (c << sh) : ((c + 1) << sh) - qi[b]);
+            Alim[b] = __int2float_rn(neg ? qi[b] : (1 << kDepth) - qi[b]);
             exit_time<QZ>(Af[b], ph[b], pl[b], ih[b], il[b], th[b], tl[b]);
-            cE = fmaxf(cE, fabsf(ih[b]) * kEA);
+            cE = fmaxf(cE, ih[b] * kEA);
         }
     }
-    uint32_t j = dl[0] | dl[1] | dl[2];
+    if (LOCK) Alim[1] = __fadd_rn(Alim[1], fsize);  // y is tested on A_x after x has stepped
+    uint32_t j = (dl[0] & dl[1] & dl[2]) ^ xm;
     float tih = 0.f, til = 0.f;
-    const int icap = (int)min(cap, (long long)0x7fffffff);
-    for (int step = 0;; ++step) {
-        if (step >= icap) return RT_ERR_STEP_LIMIT;
+    const uint32_t lim = wc.nseg + (uint32_t)min(cap, (long long)0x7fffffff);
+    for (;;) {
+        if (wc.nseg >= lim) return RT_ERR_STEP_LIMIT;
         vis.pre(j);
         int bs;
         unsigned E;
@@ -555,18 +587,19 @@ __device__ __forceinline__ int walk_f32k_grid(const DevTree& t, const DirConst* 
             if (VM == 3) {
                 E = 3u;
                 bs = 0;
-            } else if (__fsub_rn(th[2], th[0]) > (fabsf(th[2]) + fabsf(th[0])) * kER + 2.f * cE) {
+            } else if (__fsub_rn(th[2], th[0]) > (th[2] + th[0]) * kER + 2.f * cE) {
                 E = 3u;
                 bs = 0;
-            } else if (__fsub_rn(th[0], th[2]) > (fabsf(th[2]) + fabsf(th[0])) * kER + 2.f * cE) {
+            } else if (__fsub_rn(th[0], th[2]) > (th[2] + th[0]) * kER + 2.f * cE) {
                 E = 4u;
                 bs = 2;
             } else {
-                E = resolve_exit<VM>(th, Af, qf, ih, flags, dp, th[2] < th[0] ? 2 : 0, wc);
+                float thl[3] = {th[0], th[0], th[2]}, Afl[3] = {Af[0], Af[0], Af[2]};
+                E = resolve_exit<VM, true>(thl, Afl, qf, ih, flags, dp, th[2] < th[0] ? 2 : 0, wc);
                 bs = __ffs(E) - 1;
             }
         } else {
-            E = exit_set<VM, QZ>(th, Af, qf, ih, flags, cE, dp, bs, wc);
+            E = exit_set<VM, QZ, true>(th, Af, qf, ih, flags, cE, dp, bs, wc);
         }
         const float ths = sel3(th, bs), tls = sel3(tl, bs);
         const float ds = __fmul_rn(__fadd_rn(__fsub_rn(ths, tih), __fsub_rn(tls, til)), 0x1p-21f);
@@ -578,22 +611,18 @@ __device__ __forceinline__ int walk_f32k_grid(const DevTree& t, const DirConst* 
 #pragma unroll
         for (int b = 0; b < 3; b++) {
             if ((VM & (1 << b)) && (E & (1u << b))) {
-                const int pos = (flags >> (3 + b)) & 1;
-                if (c[b] == (pos ? N1 : 0)) leaving = true;
-                c[b] += pos ? 1 : -1;
-                Af[b] = __fadd_rn(Af[b], pos ? (float)size : -(float)size);
                 if (LOCK && b == 1) {
-                    th[1] = th[0];  // equal |A| and |inv|: the same exit time
-                    tl[1] = tl[0];
+                    leaving |= Af[0] == Alim[1];  // y moves with x, whose A has already grown
                 } else {
+                    leaving |= Af[b] == Alim[b];
+                    Af[b] = __fadd_rn(Af[b], fsize);
                     exit_time<QZ>(Af[b], ph[b], pl[b], ih[b], il[b], th[b], tl[b]);
                 }
-                const uint32_t mb = kDilX << b;
-                dl[b] = pos ? (((dl[b] | ~mb) + (1u << b)) & mb) : ((dl[b] - (1u << b)) & mb);
+                dl[b] = (dl[b] + (1u << b)) | dil_holes(b);
             }
         }
         if (leaving) break;
-        j = dl[0] | dl[1] | dl[2];
+        j = (dl[0] & dl[1] & dl[2]) ^ xm;
     }
     return RT_OK;
 }
@@ -721,7 +750,7 @@ __device__ __forceinline__ int walk_f32k_tree(const DevTree& t, const DirConst* 
             }
         }
         int bs;
-        const unsigned E = exit_set<VM, QZ>(th, Af, qf, ih, flags, cE, dp, bs, wc);
+        const unsigned E = exit_set<VM, QZ, false>(th, Af, qf, ih, flags, cE, dp, bs, wc);
         float the, tle;
         exit_time<QZ>(sel3(Af, bs), sel3(ph, bs), sel3(pl, bs), sel3(ih, bs), sel3(il, bs), the, tle);
         const float ds = __fmul_rn(__fadd_rn(__fsub_rn(the, tih), __fsub_rn(tle, til)), 0x1p-21f);
