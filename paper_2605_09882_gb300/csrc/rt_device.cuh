@@ -268,10 +268,15 @@ __device__ __forceinline__ int walk_fp64(const DevTree& t, const DirConst& d,
 }
 
 // FP64 walk on a full cube of equal-level leaves, moving axes VM (compile
-// time): the same operations as walk_fp64 (t_b = (F_b - Q_b) * inv_b with the
-// exact face F_b, t_out = min, E = {t_b == t_out}, ds = t_out - t_in), but a
-// face and its exit time are recomputed only on the axes that step, and the
-// leaf index is the dilated Morton index.
+// time), in the mirrored frame of the F32-Kahan grid walk (a moving axis with
+// m_b < 0 is reflected, so every moving axis advances by one cell).  The exit
+// time of the definition, fl(fl(F_b - Q_b) inv_b), is formed as
+// fl(D_b (|inv_b| 2^-53)) with D_b = |F_b - Q_b| 2^53 an exact integer held
+// in a double: F_b - Q_b is exact on the 2^-53 lattice and the scaling by
+// 2^-53 is exact, so both round the same real product and give the same
+// double (up to the sign of a zero time).  D_b grows by the leaf size on each
+// step of its axis.  Exit times are non-negative, so their minimum and ties
+// are taken on the bit patterns as integers; ds = t_out - t_in is in FP64.
 template <int VM, class V>
 __device__ __forceinline__ int walk_fp64_grid(const DevTree& t, const DirConst* __restrict__ dp,
                                               const double* __restrict__ src, long long cap, V& vis,
@@ -279,56 +284,60 @@ __device__ __forceinline__ int walk_fp64_grid(const DevTree& t, const DirConst* 
 {
     const int sh = kDepth - t.uniform_level;
     const int N1 = (1 << t.uniform_level) - 1;
-    const double hsz = (double)(1 << sh) * 0x1p-21;  // leaf size, exact
+    const double dsz = (double)(1ll << (sh + 32));  // leaf size on the 2^-53 lattice, exact
     const int flags = __ldg(&dp->flags);
-    double Q[3], F[3], tb[3], inv[3];
-    int c[3];
-    uint32_t dl[3];
+    const long long kInf = 0x7ff0000000000000ll;
+    double D[3], inv53[3];
+    long long tb[3];  // exit times as bit patterns
+    int cm[3];        // mirrored cell coordinate
+    uint32_t dl[3], xm = 0u;
 #pragma unroll
     for (int b = 0; b < 3; b++) {
         long long q;
         if (!fixed_source(src[b], q)) return RT_ERR_SOURCE_OUTSIDE;
-        Q[b] = __dmul_rn(__ll2double_rn(q), 0x1p-53);
         const uint32_t cb = (uint32_t)(q >> 32);
         if (cb >= t.ext[b]) return RT_ERR_SOURCE_OUTSIDE;
-        c[b] = (int)(cb >> sh);
-        dl[b] = spread10((uint32_t)c[b]) << b;
-        F[b] = tb[b] = inv[b] = 0.0;
+        const int c = (int)(cb >> sh);
+        const bool neg = (VM & (1 << b)) && !((flags >> (3 + b)) & 1);
+        cm[b] = neg ? (c ^ N1) : c;
+        dl[b] = (spread10((uint32_t)cm[b]) << b) | dil_holes(b);
+        if (neg) xm |= spread10((uint32_t)N1) << b;
+        D[b] = inv53[b] = 0.0;
+        tb[b] = kInf;
         if (VM & (1 << b)) {
-            inv[b] = __ldg(&dp->inv[b]);
-            const int pos = (flags >> (3 + b)) & 1;
-            F[b] = __dmul_rn(__uint2double_rn((uint32_t)(c[b] + pos) << sh), 0x1p-21);
-            tb[b] = __dmul_rn(__dsub_rn(F[b], Q[b]), inv[b]);
+            const long long F53 = (long long)(neg ? c : c + 1) << (sh + 32);
+            D[b] = __ll2double_rn(neg ? q - F53 : F53 - q);
+            inv53[b] = __dmul_rn(fabs(__ldg(&dp->inv[b])), 0x1p-53);
+            tb[b] = __double_as_longlong(__dmul_rn(D[b], inv53[b]));
         }
     }
-    uint32_t j = dl[0] | dl[1] | dl[2];
+    uint32_t j = (dl[0] & dl[1] & dl[2]) ^ xm;
     double t_in = 0.0;
-    const int icap = (int)min(cap, (long long)0x7fffffff);
-    for (int step = 0;; ++step) {
-        if (step >= icap) return RT_ERR_STEP_LIMIT;
+    const uint32_t lim = wc.nseg + (uint32_t)min(cap, (long long)0x7fffffff);
+    for (;;) {
+        if (wc.nseg >= lim) return RT_ERR_STEP_LIMIT;
         vis.pre(j);
-        double t_out = __longlong_as_double(0x7ff0000000000000ll);
+        long long to = kInf;
 #pragma unroll
         for (int b = 0; b < 3; b++)
-            if (VM & (1 << b)) t_out = fmin(t_out, tb[b]);
+            if (VM & (1 << b)) to = min(to, tb[b]);
+        const double t_out = __longlong_as_double(to);
         vis.acc(__dsub_rn(t_out, t_in));
         wc.nseg++;
         t_in = t_out;
         bool leaving = false;
 #pragma unroll
         for (int b = 0; b < 3; b++) {
-            if ((VM & (1 << b)) && tb[b] == t_out) {
-                const int pos = (flags >> (3 + b)) & 1;
-                if (c[b] == (pos ? N1 : 0)) leaving = true;
-                c[b] += pos ? 1 : -1;
-                F[b] = __dadd_rn(F[b], pos ? hsz : -hsz);
-                tb[b] = __dmul_rn(__dsub_rn(F[b], Q[b]), inv[b]);
-                const uint32_t mb = kDilX << b;
-                dl[b] = pos ? (((dl[b] | ~mb) + (1u << b)) & mb) : ((dl[b] - (1u << b)) & mb);
+            if ((VM & (1 << b)) && tb[b] == to) {
+                leaving |= cm[b] == N1;
+                cm[b]++;
+                D[b] = __dadd_rn(D[b], dsz);
+                tb[b] = __double_as_longlong(__dmul_rn(D[b], inv53[b]));
+                dl[b] = (dl[b] + (1u << b)) | dil_holes(b);
             }
         }
         if (leaving) break;
-        j = dl[0] | dl[1] | dl[2];
+        j = (dl[0] & dl[1] & dl[2]) ^ xm;
     }
     return RT_OK;
 }
@@ -901,6 +910,23 @@ __device__ __forceinline__ int walk(const DevTree& t, const DirConst* __restrict
 
 // ------------------------------------------------------------- densities
 
+// Exact float -> double of a normal float in integer operations (sign,
+// exponent rebiased by 1023 - 127, mantissa shifted up 29 bits); zeros,
+// subnormals, infinities and NaNs take the conversion instruction.
+__device__ __forceinline__ double widen_f32(float f)
+{
+    const uint32_t u = __float_as_uint(f);
+    if (((u >> 23) & 0xffu) - 1u < 254u) {
+        const uint32_t hi = (((u & 0x7fffffffu) >> 3) + 0x38000000u) | (u & 0x80000000u);
+        return __hiloint2double((int)hi, (int)(u << 29));
+    }
+    return (double)f;
+}
+template <class T>
+__device__ __forceinline__ T from_f32(float f) { return (T)f; }
+template <>
+__device__ __forceinline__ double from_f32<double>(float f) { return widen_f32(f); }
+
 // Loads S densities of leaf j into n[0..SM) (zeros past S), widening or
 // narrowing to T.
 template <int SM, class T>
@@ -911,21 +937,21 @@ __device__ __forceinline__ void load_dens(const void* __restrict__ dens, int f64
         const float* p = (const float*)dens;
         if (S == SM) {
             if (SM == 1) {
-                n[0] = (T)__ldg(p + j);
+                n[0] = from_f32<T>(__ldg(p + j));
             } else if (SM == 2) {
                 const float2 v = __ldg((const float2*)p + j);
-                n[0] = (T)v.x; n[1] = (T)v.y;
+                n[0] = from_f32<T>(v.x); n[1] = from_f32<T>(v.y);
             } else {
 #pragma unroll
                 for (int h = 0; h < SM / 4; h++) {
                     const float4 v = __ldg((const float4*)p + (size_t)j * (SM / 4) + h);
-                    n[4 * h] = (T)v.x; n[4 * h + 1] = (T)v.y;
-                    n[4 * h + 2] = (T)v.z; n[4 * h + 3] = (T)v.w;
+                    n[4 * h] = from_f32<T>(v.x); n[4 * h + 1] = from_f32<T>(v.y);
+                    n[4 * h + 2] = from_f32<T>(v.z); n[4 * h + 3] = from_f32<T>(v.w);
                 }
             }
         } else {
 #pragma unroll
-            for (int k = 0; k < SM; k++) n[k] = (k < S) ? (T)__ldg(p + (size_t)j * S + k) : (T)0;
+            for (int k = 0; k < SM; k++) n[k] = (k < S) ? from_f32<T>(__ldg(p + (size_t)j * S + k)) : (T)0;
         }
     } else {
         const double* p = (const double*)dens;
