@@ -160,7 +160,8 @@ __device__ __forceinline__ bool fixed_source(double x, long long& q)
 // Walks one ray in FP64, the operation order of the plain definition:
 //   t_b = (F_b - Q_b) * inv_b, t_out = min_b t_b, E = {b : t_b == t_out},
 //   ds = t_out - t_in, stepped axes move to the neighbour cell, the others
-//   take floor((Q_b + t_out m_b) 2^21) clamped into the current leaf.
+//   take floor((Q_b + t_out m_b) 2^21) clamped into the current leaf (formed
+//   only when the neighbour is finer than the current leaf; see below).
 // V::seg(j, ds) receives every segment.
 template <bool UNIFORM, class V>
 __device__ __forceinline__ int walk_fp64(const DevTree& t, const DirConst& d,
@@ -245,21 +246,30 @@ __device__ __forceinline__ int walk_fp64(const DevTree& t, const DirConst& d,
             }
             j = dil;
         } else {
+            // The exit axes step; the others first take the leaf's lower
+            // corner.  Unless the leaf found there is finer than the current
+            // one it holds the whole face-adjacent cell of the current size
+            // (octree cells are aligned), hence the exit point: only a finer
+            // neighbour needs the position of the definition.
 #pragma unroll
-            for (int b = 0; b < 3; b++) {
-                if (E & (1u << b)) {
-                    c[b] = (d.flags & (8 << b)) ? lo[b] + size : lo[b] - 1;
-                } else {
-                    const double P = __dadd_rn(Q[b], __dmul_rn(t_out, d.m[b]));
-                    double f = floor(__dmul_rn(P, 0x1p21));
-                    f = fmax(f, (double)lo[b]);
-                    f = fmin(f, (double)(lo[b] + size - 1));
-                    c[b] = (uint32_t)f;
-                }
-            }
+            for (int b = 0; b < 3; b++)
+                c[b] = (E & (1u << b)) ? ((d.flags & (8 << b)) ? lo[b] + size : lo[b] - 1) : lo[b];
             uint64_t key;
             int level;
             j = lookup_leaf(t, c[0], c[1], c[2], key, level);
+            if (E != 7u && j >= 0 && (1u << (kDepth - level)) < size) {
+#pragma unroll
+                for (int b = 0; b < 3; b++) {
+                    if (!(E & (1u << b))) {
+                        const double P = __dadd_rn(Q[b], __dmul_rn(t_out, d.m[b]));
+                        double f = floor(__dmul_rn(P, 0x1p21));
+                        f = fmax(f, (double)lo[b]);
+                        f = fmin(f, (double)(lo[b] + size - 1));
+                        c[b] = (uint32_t)f;
+                    }
+                }
+                j = lookup_leaf(t, c[0], c[1], c[2], key, level);
+            }
             if (j < 0) return RT_ERR_LOOKUP_MISS;
             leaf_box(key, level, lo, size);
         }
@@ -277,11 +287,18 @@ __device__ __forceinline__ int walk_fp64(const DevTree& t, const DirConst& d,
 // double (up to the sign of a zero time).  D_b grows by the leaf size on each
 // step of its axis.  Exit times are non-negative, so their minimum and ties
 // are taken on the bit patterns as integers; ds = t_out - t_in is in FP64.
-template <int VM, class V>
+// Only the axes that step recompute their time (one FP64 add and multiply
+// each), one axis at a time.
+//
+// LOCK (VM 3 or 7): bitwise-equal |inv_x| = |inv_y| and equal D_x = D_y at the
+// source, so x and y have the same exit time for the whole walk and y steps
+// whenever x does, without a time of its own.
+template <int VM, bool LOCK, class V>
 __device__ __forceinline__ int walk_fp64_grid(const DevTree& t, const DirConst* __restrict__ dp,
                                               const double* __restrict__ src, long long cap, V& vis,
                                               WalkCounters& wc)
 {
+    constexpr int VT = LOCK ? (VM & 5) : VM;  // the axes with a time of their own
     const int sh = kDepth - t.uniform_level;
     const int N1 = (1 << t.uniform_level) - 1;
     const double dsz = (double)(1ll << (sh + 32));  // leaf size on the 2^-53 lattice, exact
@@ -304,7 +321,7 @@ __device__ __forceinline__ int walk_fp64_grid(const DevTree& t, const DirConst* 
         if (neg) xm |= spread10((uint32_t)N1) << b;
         D[b] = inv53[b] = 0.0;
         tb[b] = kInf;
-        if (VM & (1 << b)) {
+        if (VT & (1 << b)) {
             const long long F53 = (long long)(neg ? c : c + 1) << (sh + 32);
             D[b] = __ll2double_rn(neg ? q - F53 : F53 - q);
             inv53[b] = __dmul_rn(fabs(__ldg(&dp->inv[b])), 0x1p-53);
@@ -320,26 +337,56 @@ __device__ __forceinline__ int walk_fp64_grid(const DevTree& t, const DirConst* 
         long long to = kInf;
 #pragma unroll
         for (int b = 0; b < 3; b++)
-            if (VM & (1 << b)) to = min(to, tb[b]);
+            if (VT & (1 << b)) to = min(to, tb[b]);
         const double t_out = __longlong_as_double(to);
         vis.acc(__dsub_rn(t_out, t_in));
         wc.nseg++;
         t_in = t_out;
-        bool leaving = false;
+        unsigned E = 0u;
 #pragma unroll
-        for (int b = 0; b < 3; b++) {
-            if ((VM & (1 << b)) && tb[b] == to) {
-                leaving |= cm[b] == N1;
-                cm[b]++;
-                D[b] = __dadd_rn(D[b], dsz);
-                tb[b] = __double_as_longlong(__dmul_rn(D[b], inv53[b]));
-                dl[b] = (dl[b] + (1u << b)) | dil_holes(b);
+        for (int b = 0; b < 3; b++)
+            if ((VT & (1 << b)) && tb[b] == to) E |= 1u << b;
+        bool leaving = false;
+        do {
+            const int s = __ffs(E) - 1;
+            E &= E - 1u;
+            const double Ds = __dadd_rn(sel3(D, s), dsz);
+            const long long ts = __double_as_longlong(__dmul_rn(Ds, sel3(inv53, s)));
+#pragma unroll
+            for (int b = 0; b < 3; b++) {
+                if ((VM & (1 << b)) && (b == s || (LOCK && b == 1 && s == 0))) {
+                    leaving |= cm[b] == N1;
+                    cm[b]++;
+                    dl[b] = (dl[b] + (1u << b)) | dil_holes(b);
+                    if (VT & (1 << b)) {
+                        D[b] = Ds;
+                        tb[b] = ts;
+                    }
+                }
             }
-        }
+        } while (E);
         if (leaving) break;
         j = (dl[0] & dl[1] & dl[2]) ^ xm;
     }
     return RT_OK;
+}
+
+// True when the x and y exit times of an FP64 grid walk stay equal: both axes
+// move, |inv_x| = |inv_y| bitwise, and the source's mirrored distances to its
+// leaf's far x and y faces are equal on the 2^-53 lattice.
+__device__ __forceinline__ bool xy_locked_fp64(const DevTree& t, int flags, const double* __restrict__ src)
+{
+    if ((flags & 3) != 3 || !inv_equal(flags, 0, 1)) return false;
+    long long q[2];
+    if (!fixed_source(src[0], q[0]) || !fixed_source(src[1], q[1])) return false;
+    const int sh = kDepth - t.uniform_level;
+    long long Dm[2];
+#pragma unroll
+    for (int b = 0; b < 2; b++) {
+        const long long c = q[b] >> (sh + 32);
+        Dm[b] = ((flags >> (3 + b)) & 1) ? ((c + 1) << (sh + 32)) - q[b] : q[b] - (c << (sh + 32));
+    }
+    return Dm[0] == Dm[1];
 }
 
 // ================================================= F32-Kahan walk (MODE 1)
@@ -706,9 +753,11 @@ __device__ __forceinline__ long long find_leaf(const DevTree& t, const uint32_t 
 }
 
 // Walk of one ray through a general octree, F32-Kahan arithmetic, moving axes
-// VM (compile time).  Exit decisions as in walk_f32k_grid; the next leaf is
-// looked up at the FP32 position of the non-stepped axes when its certified
-// interval lies inside the leaf found, else at the FP64 position.
+// VM (compile time).  Exit decisions as in walk_f32k_grid.  The next leaf is
+// looked up at the lower corner of the current leaf on the non-stepped axes;
+// only when that neighbour is finer, at the FP32 position of the non-stepped
+// axes when its certified interval lies inside the leaf found, else at the
+// FP64 position.
 template <int VM, bool QZ, class V>
 __device__ __forceinline__ int walk_f32k_tree(const DevTree& t, const DirConst* __restrict__ dp,
                                               const double* __restrict__ src, long long cap, V& vis,
@@ -767,62 +816,78 @@ __device__ __forceinline__ int walk_f32k_tree(const DevTree& t, const DirConst* 
         til = tle;
         vis.acc(ds);
         wc.nseg++;
-        // step the exit axes, position the others on a certified interval
-        const float ihe = sel3(ih, bs);
-        bool leaving = false, wide = false;
-        uint32_t chi[3];
+        // Step the exit axes; a moving axis that does not step first takes the
+        // leaf's lower corner.  The leaf found there is the neighbour of the
+        // definition unless it is finer than the current leaf: a leaf at least
+        // as large covers the whole face-adjacent cell of the current size
+        // (octree cells are aligned), so any exit point on the face lands in it.
+        bool leaving = false;
 #pragma unroll
         for (int b = 0; b < 3; b++) {
             const int pos = (flags >> (3 + b)) & 1;
             if ((VM & (1 << b)) && (E & (1u << b))) {
                 if (pos ? (lo[b] + size >= t.ext[b]) : (lo[b] == 0)) leaving = true;
                 c[b] = pos ? lo[b] + size : lo[b] - 1;
-                chi[b] = c[b];
             } else if (!(VM & (1 << b))) {
                 c[b] = (uint32_t)qi[b];  // a fixed coordinate stays inside every leaf on the path
-                chi[b] = c[b];
             } else {
-                const uint32_t hib = lo[b] + size - 1;
-                const float mw = __fmul_rn(the, m32[b]);
-                const float w = QZ ? mw : __fadd_rn(mw, ph[b]);
-                const float del = (fabsf(mw) + fabsf(w)) * 0x1p-21f + fabsf(m32[b]) * fabsf(ihe) * 0x1p-22f +
-                                  0x1p-22f;
-                // |w| + del < 2^22: floor by adding 1.5 * 2^23 rounded down
-                const int l0 = qi[b] + floor_small(__fsub_rd(w, del));
-                const int l1 = qi[b] + floor_small(__fadd_ru(w, del));
-                c[b] = (uint32_t)min(max(l0, (int)lo[b]), (int)hib);
-                chi[b] = (uint32_t)min(max(l1, (int)lo[b]), (int)hib);
-                wide |= chi[b] != c[b];
+                c[b] = lo[b];
             }
         }
         if (leaving) break;
         const uint32_t size0 = size;  // the current leaf's size
         j = find_leaf(t, c, level);
         size = 1u << (kDepth - level);
-        if (wide && j >= 0) {
-#pragma unroll
-            for (int b = 0; b < 3; b++)
-                if (chi[b] >= (c[b] & ~(size - 1u)) + size) j = -2;
-        }
-        if (j == -2 || (j < 0 && wide)) {
-            // FP64 position of the definition: floor((Q + t_out m) 2^21)
-            wc.lookup_fb++;
-            const long long De = ((long long)small_float_to_int(sel3(Af, bs)) << 32) - (long long)sel3(qf, bs);
-            const double te = __dmul_rn(__dmul_rn(__ll2double_rn(De), 0x1p-53), __ldg(&dp->inv[bs]));
+        if ((VM & ~E) != 0u && j >= 0 && size < size0) {
+            // a finer neighbour: position the moving non-exit axes on a
+            // certified interval around the exit point
+            const float ihe = sel3(ih, bs);
+            bool wide = false;
+            uint32_t chi[3];
 #pragma unroll
             for (int b = 0; b < 3; b++) {
+                chi[b] = c[b];
                 if ((VM & (1 << b)) && !(E & (1u << b))) {
-                    const long long qb = ((long long)qi[b] << 32) | (long long)qf[b];
-                    const double Qb = __dmul_rn(__ll2double_rn(qb), 0x1p-53);
-                    const double P = __dadd_rn(Qb, __dmul_rn(te, __ldg(&dp->m[b])));
-                    double f = floor(__dmul_rn(P, 0x1p21));
-                    f = fmax(f, (double)lo[b]);
-                    f = fmin(f, (double)(lo[b] + size0 - 1));
-                    c[b] = (uint32_t)f;
+                    const uint32_t hib = lo[b] + size0 - 1;
+                    const float mw = __fmul_rn(the, m32[b]);
+                    const float w = QZ ? mw : __fadd_rn(mw, ph[b]);
+                    const float del = (fabsf(mw) + fabsf(w)) * 0x1p-21f + fabsf(m32[b]) * fabsf(ihe) * 0x1p-22f +
+                                      0x1p-22f;
+                    // |w| + del < 2^22: floor by adding 1.5 * 2^23 rounded down
+                    const int l0 = qi[b] + floor_small(__fsub_rd(w, del));
+                    const int l1 = qi[b] + floor_small(__fadd_ru(w, del));
+                    c[b] = (uint32_t)min(max(l0, (int)lo[b]), (int)hib);
+                    chi[b] = (uint32_t)min(max(l1, (int)lo[b]), (int)hib);
+                    wide |= chi[b] != c[b];
                 }
             }
             j = find_leaf(t, c, level);
             size = 1u << (kDepth - level);
+            if (wide && j >= 0) {
+#pragma unroll
+                for (int b = 0; b < 3; b++)
+                    if (chi[b] >= (c[b] & ~(size - 1u)) + size) j = -2;
+            }
+            if (j == -2 || (j < 0 && wide)) {
+                // FP64 position of the definition: floor((Q + t_out m) 2^21)
+                wc.lookup_fb++;
+                const long long De = ((long long)small_float_to_int(sel3(Af, bs)) << 32) - (long long)sel3(qf, bs);
+                const double te = __dmul_rn(__dmul_rn(__ll2double_rn(De), 0x1p-53), __ldg(&dp->inv[bs]));
+#pragma unroll
+                for (int b = 0; b < 3; b++) {
+                    if ((VM & (1 << b)) && !(E & (1u << b))) {
+                        const long long qb = ((long long)qi[b] << 32) | (long long)qf[b];
+                        const double Qb = __dmul_rn(__ll2double_rn(qb), 0x1p-53);
+                        const double P = __dadd_rn(Qb, __dmul_rn(te, __ldg(&dp->m[b])));
+                        double f = floor(__dmul_rn(P, 0x1p21));
+                        f = fmax(f, (double)lo[b]);
+                        f = fmin(f, (double)(lo[b] + size0 - 1));
+                        c[b] = (uint32_t)f;
+                    }
+                }
+                j = find_leaf(t, c, level);
+                size = 1u << (kDepth - level);
+            }
         }
         if (j < 0) return RT_ERR_LOOKUP_MISS;
 #pragma unroll
@@ -888,14 +953,19 @@ __device__ __forceinline__ int walk(const DevTree& t, const DirConst* __restrict
 {
     if (MODE == RT_MODE_FP64) {
         if (UNIFORM) {
-            switch (__ldg(&dp->flags) & 7) {
-            case 1: return walk_fp64_grid<1>(t, dp, src, cap, vis, wc);
-            case 2: return walk_fp64_grid<2>(t, dp, src, cap, vis, wc);
-            case 3: return walk_fp64_grid<3>(t, dp, src, cap, vis, wc);
-            case 4: return walk_fp64_grid<4>(t, dp, src, cap, vis, wc);
-            case 5: return walk_fp64_grid<5>(t, dp, src, cap, vis, wc);
-            case 6: return walk_fp64_grid<6>(t, dp, src, cap, vis, wc);
-            default: return walk_fp64_grid<7>(t, dp, src, cap, vis, wc);
+            const int fl = __ldg(&dp->flags);
+            if (((fl & 7) == 3 || (fl & 7) == 7) && xy_locked_fp64(t, fl, src)) {
+                if ((fl & 7) == 3) return walk_fp64_grid<3, true>(t, dp, src, cap, vis, wc);
+                return walk_fp64_grid<7, true>(t, dp, src, cap, vis, wc);
+            }
+            switch (fl & 7) {
+            case 1: return walk_fp64_grid<1, false>(t, dp, src, cap, vis, wc);
+            case 2: return walk_fp64_grid<2, false>(t, dp, src, cap, vis, wc);
+            case 3: return walk_fp64_grid<3, false>(t, dp, src, cap, vis, wc);
+            case 4: return walk_fp64_grid<4, false>(t, dp, src, cap, vis, wc);
+            case 5: return walk_fp64_grid<5, false>(t, dp, src, cap, vis, wc);
+            case 6: return walk_fp64_grid<6, false>(t, dp, src, cap, vis, wc);
+            default: return walk_fp64_grid<7, false>(t, dp, src, cap, vis, wc);
             }
         }
         const DirConst d = *dp;
@@ -910,17 +980,20 @@ __device__ __forceinline__ int walk(const DevTree& t, const DirConst* __restrict
 
 // ------------------------------------------------------------- densities
 
-// Exact float -> double of a normal float in integer operations (sign,
-// exponent rebiased by 1023 - 127, mantissa shifted up 29 bits); zeros,
-// subnormals, infinities and NaNs take the conversion instruction.
+// Exact float -> double in integer operations: sign, exponent rebiased by
+// 1023 - 127 and the mantissa shifted up 29 bits; a subnormal is first scaled
+// by 2^24 in FP32 (exact) and rebiased 24 less; zeros, infinities and NaNs
+// keep their class.  No instruction of the FP64 pipe is issued.
 __device__ __forceinline__ double widen_f32(float f)
 {
     const uint32_t u = __float_as_uint(f);
-    if (((u >> 23) & 0xffu) - 1u < 254u) {
-        const uint32_t hi = (((u & 0x7fffffffu) >> 3) + 0x38000000u) | (u & 0x80000000u);
-        return __hiloint2double((int)hi, (int)(u << 29));
-    }
-    return (double)f;
+    const uint32_t a = u & 0x7fffffffu;
+    const bool sub = a < 0x00800000u;
+    const uint32_t un = sub ? __float_as_uint(__fmul_rn(__uint_as_float(a), 0x1p24f)) : a;
+    uint32_t hi = (un >> 3) + (sub ? 0x38000000u - (24u << 20) : 0x38000000u);
+    hi = (a >= 0x7f800000u) ? ((a >> 3) | 0x7ff00000u) : hi;
+    hi = (a == 0u) ? 0u : hi;
+    return __hiloint2double((int)(hi | (u & 0x80000000u)), (int)(un << 29));
 }
 template <class T>
 __device__ __forceinline__ T from_f32(float f) { return (T)f; }
