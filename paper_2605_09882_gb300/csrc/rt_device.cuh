@@ -330,9 +330,8 @@ __device__ __forceinline__ int walk_fp64_grid(const DevTree& t, const DirConst* 
     }
     uint32_t j = (dl[0] & dl[1] & dl[2]) ^ xm;
     double t_in = 0.0;
-    const uint32_t lim = wc.nseg + (uint32_t)min(cap, (long long)0x7fffffff);
+    const uint32_t lim = wc.nseg + (uint32_t)min(cap, (long long)0x7fffffff);  // cap >= 1
     for (;;) {
-        if (wc.nseg >= lim) return RT_ERR_STEP_LIMIT;
         vis.pre(j);
         long long to = kInf;
 #pragma unroll
@@ -365,7 +364,10 @@ __device__ __forceinline__ int walk_fp64_grid(const DevTree& t, const DirConst* 
                 }
             }
         } while (E);
-        if (leaving) break;
+        if (leaving || wc.nseg >= lim) {  // the cap ends a ray that still goes on
+            if (leaving) break;
+            return RT_ERR_STEP_LIMIT;
+        }
         j = (dl[0] & dl[1] & dl[2]) ^ xm;
     }
     return RT_OK;
@@ -618,8 +620,9 @@ __device__ __forceinline__ int walk_f32k_grid(const DevTree& t, const DirConst* 
         if (neg) xm |= spread10((uint32_t)N1) << b;
         Af[b] = Alim[b] = th[b] = tl[b] = ih[b] = il[b] = 0.f;
         if (VM & (1 << b)) {
-            ih[b] = fabsf(__ldg(&dp->ih[b]));
-            il[b] = neg ? -__ldg(&dp->il[b]) : __ldg(&dp->il[b]);
+            // times in box lengths: ih and il scaled by 2^-21 (exact)
+            ih[b] = fabsf(__ldg(&dp->ih[b])) * 0x1p-21f;
+            il[b] = (neg ? -__ldg(&dp->il[b]) : __ldg(&dp->il[b])) * 0x1p-21f;
             if (neg) {
                 ph[b] = -ph[b];
                 pl[b] = -pl[b];
@@ -633,9 +636,8 @@ __device__ __forceinline__ int walk_f32k_grid(const DevTree& t, const DirConst* 
     if (LOCK) Alim[1] = __fadd_rn(Alim[1], fsize);  // y is tested on A_x after x has stepped
     uint32_t j = (dl[0] & dl[1] & dl[2]) ^ xm;
     float tih = 0.f, til = 0.f;
-    const uint32_t lim = wc.nseg + (uint32_t)min(cap, (long long)0x7fffffff);
+    const uint32_t lim = wc.nseg + (uint32_t)min(cap, (long long)0x7fffffff);  // cap >= 1
     for (;;) {
-        if (wc.nseg >= lim) return RT_ERR_STEP_LIMIT;
         vis.pre(j);
         int bs;
         unsigned E;
@@ -658,7 +660,7 @@ __device__ __forceinline__ int walk_f32k_grid(const DevTree& t, const DirConst* 
             E = exit_set<VM, QZ, true>(th, Af, qf, ih, flags, cE, dp, bs, wc);
         }
         const float ths = sel3(th, bs), tls = sel3(tl, bs);
-        const float ds = __fmul_rn(__fadd_rn(__fsub_rn(ths, tih), __fsub_rn(tls, til)), 0x1p-21f);
+        const float ds = __fadd_rn(__fsub_rn(ths, tih), __fsub_rn(tls, til));
         tih = ths;
         til = tls;
         vis.acc(ds);
@@ -677,7 +679,10 @@ __device__ __forceinline__ int walk_f32k_grid(const DevTree& t, const DirConst* 
                 dl[b] = (dl[b] + (1u << b)) | dil_holes(b);
             }
         }
-        if (leaving) break;
+        if (leaving || wc.nseg >= lim) {  // the cap ends a ray that still goes on
+            if (leaving) break;
+            return RT_ERR_STEP_LIMIT;
+        }
         j = (dl[0] & dl[1] & dl[2]) ^ xm;
     }
     return RT_OK;

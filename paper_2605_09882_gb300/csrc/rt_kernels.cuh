@@ -30,7 +30,9 @@ namespace rt {
 // known (the density gather is issued there) and acc(ds) once the segment
 // length is known; seg(j, ds) does both at once.
 
-template <int SM>
+// EX: the densities are known to be FP32 with exactly SM species, so the
+// gather needs no per-segment dtype or count test.
+template <int SM, bool EX = false>
 struct FwdKahan {  // FP32 columns with Kahan compensation
     float sum[SM], cmp[SM], n[SM];
     const void* dens;
@@ -40,7 +42,11 @@ struct FwdKahan {  // FP32 columns with Kahan compensation
 #pragma unroll
         for (int k = 0; k < SM; k++) sum[k] = cmp[k] = 0.f;
     }
-    __device__ __forceinline__ void pre(uint32_t j) { load_dens<SM, float>(dens, f64, S, j, n); }
+    __device__ __forceinline__ void pre(uint32_t j)
+    {
+        if (EX) load_dens<SM, float>(dens, 0, SM, j, n);
+        else load_dens<SM, float>(dens, f64, S, j, n);
+    }
     template <class F>
     __device__ __forceinline__ void acc(F dsin)
     {
@@ -57,7 +63,7 @@ struct FwdKahan {  // FP32 columns with Kahan compensation
     __device__ __forceinline__ void seg(uint32_t j, F ds) { pre(j); acc(ds); }
 };
 
-template <int SM>
+template <int SM, bool EX = false>
 struct FwdF64 {  // FP64 columns, plain summation in path order
     double col[SM], n[SM];
     const void* dens;
@@ -67,7 +73,11 @@ struct FwdF64 {  // FP64 columns, plain summation in path order
 #pragma unroll
         for (int k = 0; k < SM; k++) col[k] = 0.0;
     }
-    __device__ __forceinline__ void pre(uint32_t j) { load_dens<SM, double>(dens, f64, S, j, n); }
+    __device__ __forceinline__ void pre(uint32_t j)
+    {
+        if (EX) load_dens<SM, double>(dens, 0, SM, j, n);
+        else load_dens<SM, double>(dens, f64, S, j, n);
+    }
     template <class F>
     __device__ __forceinline__ void acc(F dsin)
     {
@@ -167,6 +177,38 @@ __device__ __forceinline__ void ray_epilogue(const TraceArgs& a, long long s, lo
         out[ray] = exp(-a.epi_a * N);
     }
 }
+// Forward columns of one ray, stored as [ray][S].
+template <int MODE, bool UNIFORM, int SM, bool EX>
+__device__ __forceinline__ void forward_ray(const TraceArgs& a, const DirConst* d, const double* src,
+                                            long long cap, long long ray, WalkCounters& wc)
+{
+    if (MODE == RT_MODE_FP64) {
+        FwdF64<SM, EX> v;
+        v.dens = a.dens; v.f64 = a.dens_f64; v.S = a.S;
+        v.init();
+        const int st = walk<MODE, UNIFORM>(a.t, d, src, cap, v, wc);
+        if (st != RT_OK) { report_fault(a.st, st, ray); v.init(); }
+        double* o = (double*)a.out + (size_t)ray * a.S;
+#pragma unroll
+        for (int k = 0; k < SM; k++)
+            if (k < a.S) o[k] = v.col[k];
+    } else {
+        FwdKahan<SM, EX> v;
+        v.dens = a.dens; v.f64 = a.dens_f64; v.S = a.S;
+        v.init();
+        const int st = walk<MODE, UNIFORM>(a.t, d, src, cap, v, wc);
+        if (st != RT_OK) { report_fault(a.st, st, ray); v.init(); }
+        float* o = (float*)a.out + (size_t)ray * a.S;
+        if (SM == 4 && a.S == 4) {
+            *(float4*)o = make_float4(v.sum[0], v.sum[1], v.sum[2], v.sum[3]);
+        } else {
+#pragma unroll
+            for (int k = 0; k < SM; k++)
+                if (k < a.S) o[k] = v.sum[k];
+        }
+    }
+}
+
 template <int KIND, int MODE, bool UNIFORM, int SM>
 __global__ void __launch_bounds__(256, (MODE == RT_MODE_F32_KAHAN) ? (UNIFORM ? RT_MIN_BLOCKS_GRID : RT_MIN_BLOCKS_TREE)
                                                                 : RT_MIN_BLOCKS)
@@ -201,31 +243,8 @@ k_trace(const TraceArgs a)
             const double* src = a.src + 3 * s;
             WalkCounters wc = {0u, 0u, 0u};
             if (KIND == 0) {
-                if (MODE == RT_MODE_FP64) {
-                    FwdF64<SM> v;
-                    v.dens = a.dens; v.f64 = a.dens_f64; v.S = a.S;
-                    v.init();
-                    const int st = walk<MODE, UNIFORM>(a.t, d, src, cap, v, wc);
-                    if (st != RT_OK) { report_fault(a.st, st, ray); v.init(); }
-                    double* o = (double*)a.out + (size_t)ray * a.S;
-#pragma unroll
-                    for (int k = 0; k < SM; k++)
-                        if (k < a.S) o[k] = v.col[k];
-                } else {
-                    FwdKahan<SM> v;
-                    v.dens = a.dens; v.f64 = a.dens_f64; v.S = a.S;
-                    v.init();
-                    const int st = walk<MODE, UNIFORM>(a.t, d, src, cap, v, wc);
-                    if (st != RT_OK) { report_fault(a.st, st, ray); v.init(); }
-                    float* o = (float*)a.out + (size_t)ray * a.S;
-                    if (SM == 4 && a.S == 4) {
-                        *(float4*)o = make_float4(v.sum[0], v.sum[1], v.sum[2], v.sum[3]);
-                    } else {
-#pragma unroll
-                        for (int k = 0; k < SM; k++)
-                            if (k < a.S) o[k] = v.sum[k];
-                    }
-                }
+                if (!a.dens_f64 && a.S == SM) forward_ray<MODE, UNIFORM, SM, true>(a, d, src, cap, ray, wc);
+                else forward_ray<MODE, UNIFORM, SM, false>(a, d, src, cap, ray, wc);
             } else if (KIND == 1) {
                 PathHash v;
                 v.init();
