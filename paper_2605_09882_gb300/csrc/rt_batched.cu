@@ -39,8 +39,13 @@ struct BatchArgs {
 
 constexpr int kSmemClouds = 1024;  // ray offsets kept in shared memory up to this many clouds
 
+// Resident 256-thread blocks per SM the register budget is sized for.
+#ifndef RT_MIN_BLOCKS_BATCHED
+#define RT_MIN_BLOCKS_BATCHED 3
+#endif
+
 template <int MODE, int SM>
-__global__ void __launch_bounds__(256) k_batched(const BatchArgs b)
+__global__ void __launch_bounds__(256, RT_MIN_BLOCKS_BATCHED) k_batched(const BatchArgs b)
 {
     __shared__ unsigned long long s_off[kSmemClouds + 1];
     const bool in_smem = b.n_clouds <= kSmemClouds;
