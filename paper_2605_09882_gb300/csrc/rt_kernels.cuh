@@ -8,15 +8,14 @@
 
 #include "rt_device.cuh"
 
-// Resident 256-thread blocks per SM the register budget is sized for: the
-// uniform-grid F32-Kahan walk runs best at 64 registers (4 blocks), the
-// general-octree one at 85 (3 blocks); the FP64 walks keep the compiler's
-// choice.
+// Resident 256-thread blocks per SM the register budget is sized for: both
+// F32-Kahan walks run best at 64 registers (4 blocks); the FP64 walks keep
+// the compiler's choice.
 #ifndef RT_MIN_BLOCKS_GRID
 #define RT_MIN_BLOCKS_GRID 4
 #endif
 #ifndef RT_MIN_BLOCKS_TREE
-#define RT_MIN_BLOCKS_TREE 3
+#define RT_MIN_BLOCKS_TREE 4
 #endif
 #ifndef RT_MIN_BLOCKS
 #define RT_MIN_BLOCKS 1
