@@ -29,6 +29,7 @@ sys.path.insert(0, ROOT)
 BYTES_PER_SEGMENT = 8 + 1 + 4 * 4  # key + level + 4 FP32 densities (algorithmic)
 NSIDE = 1
 LEVEL = 9
+E2E_CHUNK = 1 << 23  # sources per pipeline chunk of the host-buffer call (16 chunks at 512^3)
 METRIC = "ray-segments/s at 512^3 Nside=1 (FP32-Kahan vs FP64 @1e-5 rel); adjoint/fwd time"
 
 
@@ -517,25 +518,24 @@ def main():
         h2d = sum(t.numel() * t.element_size() for t in (keys_p, lev_p, dens_p, src_p))
         d2h = out_p.numel() * out_p.element_size()
         e2e_steps = 2
+        # one untimed call sizes the call's persistent device buffers
+        rt.trace_columns_host(keys_p, lev_p, src_p, NSIDE, dens_p, "f32k", out=out_p, chunk=E2E_CHUNK)
         barrier()
         t0 = time.perf_counter()
         e0.record(stream)
         for _ in range(e2e_steps):
-            kd = keys_p.to(dev, non_blocking=True)
-            ld = lev_p.to(dev, non_blocking=True)
-            dd = dens_p.to(dev, non_blocking=True)
-            sd = src_p.to(dev, non_blocking=True)
-            t2 = rt.Octree(kd, ld)
-            rt.trace_columns(t2, sd, NSIDE, dd, "f32k", out=out)
-            out_p.copy_(out, non_blocking=True)
-            torch.cuda.synchronize()
-            t2.close()
+            # one C-ABI call: host buffers in, octree indexed, columns back,
+            # copies pipelined with the traces in source chunks
+            _, st_e2e = rt.trace_columns_host(keys_p, lev_p, src_p, NSIDE, dens_p, "f32k", out=out_p,
+                                              chunk=E2E_CHUNK)
+            assert st_e2e["status"] == 0 and st_e2e["segments"] == seg_per_step, st_e2e
         e1.record(stream)
         barrier()
         wall = time.perf_counter() - t0
         e2e = {"value": world * seg_per_step * e2e_steps / wall, "unit": "ray-segments/s",
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-               "ms_per_step": wall * 1e3 / e2e_steps}
+               "ms_per_step": wall * 1e3 / e2e_steps,
+               "call": f"rt_trace_columns_host, page-locked host buffers, {E2E_CHUNK} sources per chunk"}
 
     line = {
         "metric": METRIC,

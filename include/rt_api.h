@@ -124,6 +124,36 @@ int rt_trace_columns(const rt_octree* tree, const double* d_src, int64_t n_src, 
                      const void* d_dens, int n_species, int dens_dtype, int mode,
                      void* d_out, void* stream);
 
+/* Forward trace (Sec. 2.2) end to end from HOST buffers: copies the octree,
+ * densities and sources to the device, indexes the octree (as
+ * rt_build_octree), traces, and copies the columns back; returns when h_out
+ * is written.
+ *   h_keys, h_levels, n_leaves, h_extent: as rt_build_octree, in host memory.
+ *   h_src: host float64 [n_src][3].  h_dens: host [n_leaves][n_species] of
+ *     dens_dtype.  h_out: host [n_src][12 nside^2][n_species], float32 for
+ *     RT_MODE_F32_KAHAN, float64 for RT_MODE_FP64.
+ *   chunk_src: sources per pipeline chunk (0: about n_src / 8); rounded up to
+ *     a multiple of 32 and to at most 1024 chunks.  Chunk c's source copy,
+ *     trace and column copy run on separate streams, so copies overlap the
+ *     traces of neighbouring chunks; page-locked host buffers (cudaHostAlloc
+ *     or cudaHostRegister) let the copies run as DMA.
+ *   h_stats: optional; receives the trace's statistics.
+ *   stream: the stream the traces run on (two more are created inside).
+ * Device buffers (the octree, densities, all sources and two column
+ * chunks), the two copy streams and the events are kept per device between
+ * calls and grow on demand; rt_trace_columns_host_release frees them.  Calls
+ * are serialized by a process-wide lock.  Returns RT_ERR_OOM if the buffers
+ * do not fit, the code of the first faulting ray if a ray faulted (its
+ * columns are zero), and the rt_build_octree codes for a malformed octree. */
+int rt_trace_columns_host(const uint64_t* h_keys, const uint8_t* h_levels, int64_t n_leaves,
+                          const int32_t* h_extent, const double* h_src, int64_t n_src, int nside,
+                          const void* h_dens, int n_species, int dens_dtype, int mode, void* h_out,
+                          int64_t chunk_src, rt_stats* h_stats, void* stream);
+
+/* Frees the device buffers, streams and events rt_trace_columns_host keeps,
+ * on every device it used (waiting for their copies first). */
+void rt_trace_columns_host_release(void);
+
 /* Per-source quantities computed inside the trace, so that the columns are
  * never written (the paper's 3D-PDR coupling, Sec. 2.4, and its accuracy
  * test, Sec. 3).  Each ray's combined column is N = sum_k weights[k] I_k, a

@@ -91,6 +91,10 @@ def _load():
     lib.rt_paths_adjoint.argtypes = [P, P, i32, P, P]
     lib.rt_destroy_paths.argtypes = [P]
     lib.rt_destroy_paths.restype = None
+    lib.rt_trace_columns_host.argtypes = [P, P, i64, P, P, i64, i32, P, i32, i32, i32, P, i64,
+                                          C.POINTER(Stats), P]
+    lib.rt_trace_columns_host_release.argtypes = []
+    lib.rt_trace_columns_host_release.restype = None
     return lib
 
 
@@ -215,6 +219,57 @@ def trace_columns(tree: Octree, src, nside: int, dens, mode="f32k", out=None, st
                                  F64 if dens.dtype == torch.float64 else F32, m, _dptr(out),
                                  _stream(stream)))
     return out
+
+
+def trace_columns_host(keys, levels, src, nside: int, dens, mode="f32k", out=None, extent=None,
+                       chunk: int = 0, stream=None):
+    """Forward trace end to end from host (CPU) tensors: the octree, densities
+    and sources are copied in and the columns copied back inside the call,
+    in chunks that overlap the copies with the traces (page-locked tensors
+    copy fastest).  The device buffers persist between calls until
+    trace_columns_host_release().  Returns (columns, statistics dict)."""
+    import torch
+
+    def host(t, what, dtypes):
+        if isinstance(t, np.ndarray):
+            t = torch.from_numpy(t)
+        if t.device.type != "cpu" or not t.is_contiguous() or t.dtype not in dtypes:
+            raise ValueError(f"{what} must be a contiguous CPU tensor of {dtypes}")
+        return t
+
+    m = _mode(mode)
+    keys = host(keys, "keys", (torch.int64, torch.uint64))
+    levels = host(levels, "levels", (torch.uint8,))
+    src = host(src, "src", (torch.float64,))
+    dens = host(dens, "dens", (torch.float32, torch.float64))
+    if dens.dim() == 1:
+        dens = dens[:, None]
+    if src.dim() != 2 or src.shape[1] != 3:
+        raise ValueError("src must be float64 [n_src, 3]")
+    if dens.shape[0] != keys.numel() or levels.numel() != keys.numel():
+        raise ValueError("keys, levels and dens must have one row per leaf")
+    S = int(dens.shape[1])
+    nd = 12 * nside * nside
+    odt = torch.float32 if m == MODE_F32_KAHAN else torch.float64
+    if out is None:
+        out = torch.empty((src.shape[0], nd, S), dtype=odt)
+    elif (out.device.type != "cpu" or out.dtype != odt or tuple(out.shape) != (src.shape[0], nd, S)
+          or not out.is_contiguous()):
+        raise ValueError("out has the wrong device, dtype, shape or layout")
+    ext = None
+    if extent is not None:
+        ext = (C.c_int32 * 3)(*[int(e) for e in extent])
+    st = Stats()
+    _check(_lib.rt_trace_columns_host(_dptr(keys), _dptr(levels), int(keys.numel()), ext, _dptr(src),
+                                      int(src.shape[0]), int(nside), _dptr(dens), S,
+                                      F64 if dens.dtype == torch.float64 else F32, m, _dptr(out), int(chunk),
+                                      C.byref(st), _stream(stream)))
+    return out, {f: getattr(st, f) for f, _ in Stats._fields_}
+
+
+def trace_columns_host_release():
+    """Frees the device buffers trace_columns_host keeps between calls."""
+    _lib.rt_trace_columns_host_release()
 
 
 def trace_paths(tree: Octree, src, nside: int, mode="f32k", stream=None):
