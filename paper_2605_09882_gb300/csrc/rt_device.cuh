@@ -706,6 +706,15 @@ __device__ __forceinline__ bool xy_locked(const DevTree& t, int flags, const dou
 
 // ------------------------------------ F32-Kahan walk on a general octree
 
+// A float of the direction table, loaded where it is used (a volatile load,
+// so it is not hoisted into a register held across the walk).
+__device__ __forceinline__ float dir_const(const float* p)
+{
+    float v;
+    asm volatile("ld.global.nc.f32 %0, [%1];" : "=f"(v) : "l"(p));
+    return v;
+}
+
 // floor(v) for |v| < 2^22 without a conversion instruction: v + 1.5 * 2^23
 // rounded down lies in [2^23, 2^24), where floats are the integers.
 __device__ __forceinline__ int floor_small(float v)
@@ -768,8 +777,11 @@ __device__ __forceinline__ int walk_f32k_tree(const DevTree& t, const DirConst* 
                                               const double* __restrict__ src, long long cap, V& vis,
                                               WalkCounters& wc)
 {
+    // The direction's constants (ih, il, m32) are read from the direction
+    // table where they are used: one broadcast load per warp, kept out of the
+    // per-ray registers.
     const int flags = __ldg(&dp->flags);
-    float ih[3], il[3], m32[3], ph[3], pl[3], qif[3];
+    float ph[3], pl[3], qif[3];
     int qi[3];
     uint32_t qf[3], c[3];
     float cE = 0.f;
@@ -779,13 +791,7 @@ __device__ __forceinline__ int walk_f32k_tree(const DevTree& t, const DirConst* 
     for (int b = 0; b < 3; b++) {
         qif[b] = small_int_to_float((uint32_t)qi[b]);
         c[b] = (uint32_t)qi[b];
-        ih[b] = il[b] = m32[b] = 0.f;
-        if (VM & (1 << b)) {
-            ih[b] = __ldg(&dp->ih[b]);
-            il[b] = __ldg(&dp->il[b]);
-            m32[b] = __ldg(&dp->m32[b]);
-            cE = fmaxf(cE, fabsf(ih[b]) * kEA);
-        }
+        if (VM & (1 << b)) cE = fmaxf(cE, fabsf(dir_const(&dp->ih[b])) * kEA);
     }
     int level;
     long long j = find_leaf(t, c, level);
@@ -795,14 +801,15 @@ __device__ __forceinline__ int walk_f32k_tree(const DevTree& t, const DirConst* 
 #pragma unroll
     for (int b = 0; b < 3; b++) lo[b] = c[b] & ~(size - 1u);
     float tih = 0.f, til = 0.f;
-    for (long long step = 0;; ++step) {
-        if (step >= cap) return RT_ERR_STEP_LIMIT;
+    const uint32_t lim = wc.nseg + (uint32_t)min(cap, (long long)0x7fffffff);  // cap >= 1
+    for (;;) {
         vis.pre((uint32_t)j);
-        float Af[3], th[3], tl[3];
+        float Af[3], th[3], tl[3], ih[3];
 #pragma unroll
         for (int b = 0; b < 3; b++) {
-            Af[b] = th[b] = tl[b] = 0.f;
+            Af[b] = th[b] = tl[b] = ih[b] = 0.f;
             if (VM & (1 << b)) {
+                ih[b] = dir_const(&dp->ih[b]);
                 const uint32_t F = ((flags >> (3 + b)) & 1) ? lo[b] + size : lo[b];
                 Af[b] = __fsub_rn(small_int_to_float(F), qif[b]);
                 if (QZ) {
@@ -815,7 +822,7 @@ __device__ __forceinline__ int walk_f32k_tree(const DevTree& t, const DirConst* 
         int bs;
         const unsigned E = exit_set<VM, QZ, false>(th, Af, qf, ih, flags, cE, dp, bs, wc);
         float the, tle;
-        exit_time<QZ>(sel3(Af, bs), sel3(ph, bs), sel3(pl, bs), sel3(ih, bs), sel3(il, bs), the, tle);
+        exit_time<QZ>(sel3(Af, bs), sel3(ph, bs), sel3(pl, bs), sel3(ih, bs), dir_const(&dp->il[bs]), the, tle);
         const float ds = __fmul_rn(__fadd_rn(__fsub_rn(the, tih), __fsub_rn(tle, til)), 0x1p-21f);
         tih = the;
         til = tle;
@@ -854,9 +861,10 @@ __device__ __forceinline__ int walk_f32k_tree(const DevTree& t, const DirConst* 
                 chi[b] = c[b];
                 if ((VM & (1 << b)) && !(E & (1u << b))) {
                     const uint32_t hib = lo[b] + size0 - 1;
-                    const float mw = __fmul_rn(the, m32[b]);
+                    const float m32 = dir_const(&dp->m32[b]);
+                    const float mw = __fmul_rn(the, m32);
                     const float w = QZ ? mw : __fadd_rn(mw, ph[b]);
-                    const float del = (fabsf(mw) + fabsf(w)) * 0x1p-21f + fabsf(m32[b]) * fabsf(ihe) * 0x1p-22f +
+                    const float del = (fabsf(mw) + fabsf(w)) * 0x1p-21f + fabsf(m32) * fabsf(ihe) * 0x1p-22f +
                                       0x1p-22f;
                     // |w| + del < 2^22: floor by adding 1.5 * 2^23 rounded down
                     const int l0 = qi[b] + floor_small(__fsub_rd(w, del));
@@ -895,6 +903,7 @@ __device__ __forceinline__ int walk_f32k_tree(const DevTree& t, const DirConst* 
             }
         }
         if (j < 0) return RT_ERR_LOOKUP_MISS;
+        if (wc.nseg >= lim) return RT_ERR_STEP_LIMIT;  // the cap ends a ray that still goes on
 #pragma unroll
         for (int b = 0; b < 3; b++) lo[b] = c[b] & ~(size - 1u);
     }
