@@ -48,3 +48,26 @@ def test_library_rejects_bad_nside():
 def test_last_error_is_a_string():
     import paper_2605_09882_gb300 as rt
     assert isinstance(rt._lib.rt_last_error(), bytes)
+
+
+def test_host_call_rejects_bad_arguments_before_any_device_work():
+    import ctypes
+    import paper_2605_09882_gb300 as rt
+    lib = rt._lib
+    buf = ctypes.create_string_buffer(4096)
+    p = ctypes.cast(buf, ctypes.c_void_p)
+    st = rt.Stats()
+
+    def call(keys=p, levels=p, n=8, src=p, n_src=4, nside=1, dens=p, S=1, dt=0, mode=1, out=p, chunk=0):
+        return lib.rt_trace_columns_host(keys, levels, n, None, src, n_src, nside, dens, S, dt, mode, out, chunk,
+                                         ctypes.byref(st), None)
+
+    ARG = 1
+    assert call(keys=None) == ARG
+    assert call(dens=None) == ARG
+    assert call(src=None) == ARG and call(out=None) == ARG
+    assert call(n=0) == ARG and call(n_src=-1) == ARG and call(chunk=-5) == ARG
+    assert call(S=0) == ARG and call(S=9) == ARG
+    assert call(dt=3) == ARG and call(mode=2) == ARG
+    assert call(nside=0) == ARG
+    assert b"rt_trace_columns_host" in lib.rt_last_error()
