@@ -43,7 +43,7 @@ def parse():
     p.add_argument("--no-extras", action="store_true", help="skip FP64 form, adjoint, e2e, CPU baseline")
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
     p.add_argument("--workload", default="uniform512",
-                   choices=["uniform512", "amr128", "batched64", "adjoint_amr64", "dualgrid256"],
+                   choices=["uniform512", "amr128", "batched64", "adjoint_amr64", "dualgrid256", "angular128"],
                    help="uniform512 is the benchmark; the others run one secondary workload alone")
     return p.parse_args()
 
@@ -304,6 +304,119 @@ def dualgrid_leg(rt, dev, stream, level=8, reps=1):
     return res
 
 
+# ------------------------------------------------ angular convergence (Sec. 3)
+
+def ang2pix_ring(nside: int, v: np.ndarray) -> np.ndarray:
+    """HEALPix RING index of the pixel containing each unit vector v [m][3]
+    (Gorski et al. 2005 geometry).  In the equatorial belt (|z| <= 2/3) the
+    pixel edges are the lines N(1/2 + phi/(pi/2)) -+ (3N/4) z = integer, so two
+    floor indices (one per edge family) give the ring and the place in it; in
+    a polar cap the edges are tp * N sqrt(3 (1 - |z|)) = integer and
+    (1 - tp) * N sqrt(3 (1 - |z|)) = integer, tp the position inside the
+    quadrant."""
+    v = np.asarray(v, dtype=np.float64)
+    z = v[:, 2] / np.linalg.norm(v, axis=1)
+    phi = np.mod(np.arctan2(v[:, 1], v[:, 0]), 2.0 * np.pi)
+    tt = phi / (0.5 * np.pi)                       # quadrant coordinate in [0, 4)
+    n = nside
+    npix = 12 * n * n
+    out = np.empty(z.shape[0], dtype=np.int64)
+    eq = np.abs(z) <= 2.0 / 3.0
+    # equatorial belt
+    a = n * (0.5 + tt[eq])
+    b = 0.75 * n * z[eq]
+    jp = np.floor(a - b).astype(np.int64)          # index of the ascending edge below
+    jm = np.floor(a + b).astype(np.int64)          # index of the descending edge below
+    ring = n + 1 + jp - jm                         # 1 .. 2n+1, counted from z = 2/3
+    shift = 1 - (ring & 1)
+    k = np.mod((jp + jm - n + shift + 1) // 2, 4 * n)   # place in the ring, 0-based
+    out[eq] = 2 * n * (n - 1) + (ring - 1) * 4 * n + k
+    # polar caps
+    pc = ~eq
+    za = np.abs(z[pc])
+    tp = tt[pc] - np.floor(tt[pc])
+    r = n * np.sqrt(3.0 * (1.0 - za))
+    jp = np.floor(tp * r).astype(np.int64)
+    jm = np.floor((1.0 - tp) * r).astype(np.int64)
+    ring = jp + jm + 1                             # ring counted from the nearer pole
+    k = np.mod(np.floor(tt[pc] * ring).astype(np.int64), 4 * ring)
+    north = z[pc] > 0
+    out[np.flatnonzero(pc)[north]] = (2 * ring * (ring - 1) + k)[north]
+    out[np.flatnonzero(pc)[~north]] = (npix - 2 * ring * (ring + 1) + k)[~north]
+    return out
+
+
+def angular_leg(rt, dev, stream, level=7, nsides=(1, 2, 4, 8), nside_ref=64, reps=3):
+    """The paper's angular-convergence test on a synthetic 128^3 cloud (one
+    species, total hydrogen, lognormal sigma 2, 125 pc box):
+    - sky maps of N_H from the leaf centre nearest the domain centre at Nside
+      1..8 against Nside 64 (49152 rays): e_NH,q = |N_q - <N^ref>_q| / <N^ref>_q,
+      <N^ref>_q the mean of the Nside-64 columns whose directions fall in pixel q;
+    - A_V,eff of every cell at Nside 1, 2, 4 against Nside 64, computed inside
+      the trace (the fused epilogue), e_AV = |A_V - A_V^ref| / A_V^ref;
+    - the many-rays-per-source shape: 1 and 16 sources at Nside 64."""
+    import torch
+    from synth import torchgen
+    keys, lev, dens, ntot = torchgen.uniform_cloud(level, 2.0, 8, fracs=(1.0,), device=dev)
+    tree = rt.Octree(keys, lev)
+    n_cells = keys.numel()
+    box_cm = 125 * 3.0857e18
+    a_av = 6.29e-22 * box_cm
+    half = 1 << (level - 1)
+    c = torch.tensor([[half + 0.5, half + 0.5, half + 0.5]], dtype=torch.float64, device=dev) / (1 << level)
+    res = {"workload": "%d^3 uniform lognormal cloud (sigma 2), total H, 125 pc box; sky maps from the cell centre "
+                       "nearest the domain centre and A_V,eff of all %d cells, Nside %s against Nside %d"
+                       % (1 << level, n_cells, "/".join(str(x) for x in nsides), nside_ref, )}
+    # sky maps
+    ref = rt.trace_columns(tree, c, nside_ref, dens, "f32k")[0, :, 0].double().cpu().numpy()
+    dirs_ref = rt.healpix_dirs(nside_ref)
+    maps = {}
+    for ns in nsides:
+        col = rt.trace_columns(tree, c, ns, dens, "f32k")[0, :, 0].double().cpu().numpy()
+        parent = ang2pix_ring(ns, dirs_ref)
+        mean_ref = np.bincount(parent, weights=ref, minlength=12 * ns * ns) / np.bincount(parent, minlength=12 * ns * ns)
+        e = np.abs(col - mean_ref) / mean_ref
+        maps[str(ns)] = {"rays": 12 * ns * ns, "e_NH_mean": float(e.mean()), "e_NH_max": float(e.max())}
+    res["sky_map_e_NH"] = maps
+    # A_V,eff of every cell
+    src = torchgen.uniform_centres(level, torch.arange(n_cells, device=dev))
+    tree.reset_stats()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    av_ref = rt.trace_epilogue(tree, src, nside_ref, dens, "av_eff", [1.0], a_av, 3.02)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    st = tree.stats()
+    assert st["status"] == 0, st
+    t_ref = e0.elapsed_time(e1) / 1e3
+    res["av_eff_reference"] = {"nside": nside_ref, "rays": int(st["rays"]), "segments": int(st["segments"]),
+                               "seconds": t_ref, "value": st["segments"] / t_ref, "unit": "ray-segments/s",
+                               "mean_av_eff": float(av_ref.mean().item())}
+    dens_cells = ntot.double()
+    dense = dens_cells >= torch.quantile(dens_cells.float(), 0.9).double()
+    errs = {}
+    for ns in nsides[:3]:
+        av = rt.trace_epilogue(tree, src, ns, dens, "av_eff", [1.0], a_av, 3.02)
+        e = (av - av_ref).abs() / av_ref
+        errs[str(ns)] = {"e_AV_mean": float(e.mean().item()), "e_AV_max": float(e.max().item()),
+                         "e_AV_mean_densest_10pct": float(e[dense].mean().item())}
+    res["av_eff_e_AV"] = errs
+    # many rays per source: 1 and 16 sources near the centre at Nside 64
+    rates = {}
+    for m in (1, 16):
+        s_m = src[n_cells // 2: n_cells // 2 + m]
+        out = torch.empty((m, 12 * nside_ref ** 2, 1), dtype=torch.float32, device=dev)
+        tree.reset_stats()
+        t = timed(lambda: rt.trace_columns(tree, s_m, nside_ref, dens, "f32k", out=out), stream, reps=reps)
+        segs = tree.stats()["segments"] / (reps + 1)
+        rates[str(m)] = {"rays": m * 12 * nside_ref ** 2, "ms_per_trace": t * 1e3, "value": segs / t,
+                         "unit": "ray-segments/s"}
+    res["few_sources_nside64"] = rates
+    tree.close()
+    return res
+
+
+# -------------------------------------------------------------- reference
 # -------------------------------------------------------------- reference
 
 def run_reference(a, rank, world):
@@ -372,6 +485,8 @@ def main():
                             reps=a.steps)
         elif a.workload == "dualgrid256":
             r = dualgrid_leg(rt, dev, stream, reps=a.steps)
+        elif a.workload == "angular128":
+            r = angular_leg(rt, dev, stream, reps=a.steps)
         else:
             r = adjoint_leg(rt, dev, stream, reps=a.steps)
         if rank == 0:
