@@ -123,3 +123,25 @@ def test_host_call_workspace_grows_and_releases(rt):
     got, _ = rt.trace_columns_host(torch.from_numpy(keys.view(np.int64)), torch.from_numpy(lev),
                                    torch.from_numpy(src), 1, torch.from_numpy(dens), "f32k")
     rt.trace_columns_host_release()
+
+
+@pytest.mark.parametrize("mode", ["f32k", "fp64"])
+def test_host_call_extent_and_fp64_densities(rt, mode):
+    import torch
+    rng = np.random.default_rng(17)
+    keys, lev, ext = random_octree(rng, 3, 6, 0.3, extent_cells=5)
+    dens = rng.uniform(0.1, 10.0, size=(keys.shape[0], 2))  # float64 densities
+    e = np.asarray(ext, dtype=np.float64) / float(1 << 21)
+    src = rng.random((500, 3)) * e
+    tree = rt.Octree(torch.from_numpy(keys.view(np.int64)).cuda(), torch.from_numpy(lev).cuda(), extent=ext)
+    want = rt.trace_columns(tree, torch.from_numpy(src).cuda(), 2, torch.from_numpy(dens).cuda(), mode).cpu().numpy()
+    tree.close()
+    got, st = rt.trace_columns_host(torch.from_numpy(keys.view(np.int64)), torch.from_numpy(lev),
+                                    torch.from_numpy(src), 2, torch.from_numpy(dens), mode, extent=ext, chunk=128)
+    np.testing.assert_array_equal(got.numpy(), want)
+    ref, _, _ = oracle.trace(keys, lev, dens, src, oracle.healpix(2), extent=ext)
+    if mode == "fp64":
+        np.testing.assert_array_equal(got.numpy(), ref)
+    else:
+        d = np.abs(got.numpy().astype(np.float64) - ref)
+        assert (d <= RTOL * np.abs(ref) + ATOL).all()
