@@ -570,6 +570,24 @@ __device__ __forceinline__ int source_fixed(const double* __restrict__ src, cons
     return RT_OK;
 }
 
+// Exit axis b of the grid walk steps one cell: the domain-exit test, its
+// far-face distance and exit time, and its dilated index.  Under LOCK, y moves
+// with x, whose distance has already grown (x steps first).
+template <int b, bool QZ, bool LOCK>
+__device__ __forceinline__ void grid_step(float Af[3], const float Alim[3], const float ph[3], const float pl[3],
+                                          const float ih[3], const float il[3], float th[3], float tl[3],
+                                          uint32_t dl[3], float fsize, bool& leaving)
+{
+    if (LOCK && b == 1) {
+        leaving |= Af[0] == Alim[1];
+    } else {
+        leaving |= Af[b] == Alim[b];
+        Af[b] = __fadd_rn(Af[b], fsize);
+        exit_time<QZ>(Af[b], ph[b], pl[b], ih[b], il[b], th[b], tl[b]);
+    }
+    dl[b] = (dl[b] + (1u << b)) | dil_holes(b);
+}
+
 // Walk of one ray through a full cube of equal-level leaves (level L <= 10),
 // F32-Kahan arithmetic, for a direction whose moving axes are the bits of VM.
 //
@@ -666,18 +684,18 @@ __device__ __forceinline__ int walk_f32k_grid(const DevTree& t, const DirConst* 
         vis.acc(ds);
         wc.nseg++;
         bool leaving = false;
-#pragma unroll
-        for (int b = 0; b < 3; b++) {
-            if ((VM & (1 << b)) && (E & (1u << b))) {
-                if (LOCK && b == 1) {
-                    leaving |= Af[0] == Alim[1];  // y moves with x, whose A has already grown
-                } else {
-                    leaving |= Af[b] == Alim[b];
-                    Af[b] = __fadd_rn(Af[b], fsize);
-                    exit_time<QZ>(Af[b], ph[b], pl[b], ih[b], il[b], th[b], tl[b]);
-                }
-                dl[b] = (dl[b] + (1u << b)) | dil_holes(b);
-            }
+        // A warp whose lanes all take the same locked step (every lane of a
+        // leaf-centre beam does) runs only that step's body.
+        const unsigned am = (LOCK && VM == 7) ? __activemask() : 0u;
+        if (LOCK && VM == 7 && __all_sync(am, E == 4u)) {
+            grid_step<2, QZ, LOCK>(Af, Alim, ph, pl, ih, il, th, tl, dl, fsize, leaving);
+        } else if (LOCK && VM == 7 && __all_sync(am, E == 3u)) {
+            grid_step<0, QZ, LOCK>(Af, Alim, ph, pl, ih, il, th, tl, dl, fsize, leaving);
+            grid_step<1, QZ, LOCK>(Af, Alim, ph, pl, ih, il, th, tl, dl, fsize, leaving);
+        } else {
+            if ((VM & 1) && (E & 1u)) grid_step<0, QZ, LOCK>(Af, Alim, ph, pl, ih, il, th, tl, dl, fsize, leaving);
+            if ((VM & 2) && (E & 2u)) grid_step<1, QZ, LOCK>(Af, Alim, ph, pl, ih, il, th, tl, dl, fsize, leaving);
+            if ((VM & 4) && (E & 4u)) grid_step<2, QZ, LOCK>(Af, Alim, ph, pl, ih, il, th, tl, dl, fsize, leaving);
         }
         if (leaving || wc.nseg >= lim) {  // the cap ends a ray that still goes on
             if (leaving) break;
