@@ -231,3 +231,26 @@ def test_few_sources_many_directions(rt):
     cloud = synth.uniform_cloud(5, 1.0, 4, fracs=(1.0,), dtype=np.float64)
     _check_case(rt, cloud.keys, cloud.levels, cloud.dens, np.array([[0.515625, 0.515625, 0.515625]]), 16,
                 label="uniform centre nside16")
+
+
+@pytest.mark.parametrize("seed", range(2))
+def test_uniform_grid_off_lattice_sources(rt, seed):
+    """The uniform-grid walks with sources off the cell lattice (non-zero
+    fractions), on cell corners and faces, and on x = y diagonals (equal x/y
+    distances: the FP64 lock-step without zero fractions), Nside 1, 2 and 4,
+    both modes."""
+    rng = np.random.default_rng(3000 + seed)
+    keys, lev = uniform_octree(4)
+    dens = rng.uniform(0.1, 10.0, size=(keys.shape[0], 2)).astype(np.float32)
+    lo, hi = leaf_boxes(keys, lev)
+    pick = rng.choice(keys.shape[0], size=16, replace=False)
+    a, b = rng.random(24), rng.random(24)
+    pts = [rng.random((64, 3)),                                   # off the lattice
+           0.5 * (lo[pick] + hi[pick]),                           # cell centres
+           lo[pick],                                              # cell corners
+           np.column_stack([lo[pick, 0], rng.random(16), rng.random(16)]),   # on an x face
+           np.column_stack([a, a, b]),                            # x = y, off the lattice
+           np.column_stack([1.0 - a, a, b])]                      # mirrored diagonal
+    src = np.concatenate(pts)
+    for nside in (1, 2, 4):
+        _check_case(rt, keys, lev, dens, src, nside, label=f"uniform16 off-lattice {seed} nside{nside}")
