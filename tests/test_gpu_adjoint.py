@@ -50,6 +50,32 @@ def test_adjoint_matches_oracle(rt, seed):
     tree.close()
 
 
+@pytest.mark.parametrize("S", [1, 4])
+def test_uniform_grid_adjoint_matches_oracle(rt, S):
+    """The uniform-grid walks (the 512^3 bench's adjoint path): leaf centres,
+    which take the x/y-locked and zero-fraction forms, and off-lattice
+    sources, Nside 1 and 2."""
+    from tinytrees import uniform_octree
+    rng = np.random.default_rng(400 + S)
+    keys, lev = uniform_octree(4)
+    cloud = synth.Cloud(keys, lev, np.zeros((keys.shape[0], 1)), (1 << 21,) * 3)
+    src = np.concatenate([synth.leaf_centres(cloud)[::7], rng.random((100, 3))])
+    tree = rt.Octree(_dev(keys), _dev(lev))
+    for nside in (1, 2):
+        dirs = oracle.healpix(nside)
+        g = rng.standard_normal((src.shape[0], dirs.shape[0], S))
+        ref = oracle.adjoint(keys, lev, S, src, dirs, g)
+        scale = np.abs(ref).max()
+        gd = rt.trace_columns_adjoint(tree, _dev(src), nside, _dev(g), "fp64").cpu().numpy()
+        np.testing.assert_allclose(gd, ref, rtol=1e-12, atol=1e-13 * scale)
+        g32 = g.astype(np.float32)
+        gk = rt.trace_columns_adjoint(tree, _dev(src), nside, _dev(g32), "f32k").cpu().numpy()
+        refk = oracle.adjoint(keys, lev, S, src, dirs, g32.astype(np.float64))
+        np.testing.assert_allclose(gk, refk, rtol=2e-6, atol=1e-6 * scale)
+    assert tree.stats()["status"] == 0
+    tree.close()
+
+
 def test_dot_product_identity(rt):
     import torch
     rng = np.random.default_rng(11)
