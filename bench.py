@@ -571,17 +571,38 @@ def main():
                                   "mean_rel_per_species": [float(x) / (n * nd) for x in sm]}
         del rel, out64
         torch.cuda.empty_cache()
-        # ---- adjoint (F32-Kahan walk, FP64 gradient), seed = the forward output
+        # ---- adjoint (F32-Kahan walk, FP64 gradient), seed = the forward output:
+        # the default (leaf gather, deterministic) and the atomic scatter
         grad = torch.zeros((n, 4), dtype=torch.float64, device=dev)
         rt.trace_columns_adjoint(tree, src, NSIDE, out, "f32k", grad_dens=grad)
         barrier()
+        tree.reset_stats()
         e0.record(stream)
         rt.trace_columns_adjoint(tree, src, NSIDE, out, "f32k", grad_dens=grad)
         e1.record(stream)
         barrier()
         tadj = e0.elapsed_time(e1) / 1e3
-        extras["adjoint"] = {"ms_per_step": tadj * 1e3, "adjoint_over_forward": tadj / avg_launch_s}
-        del grad
+        sadj = tree.stats()
+        grad.zero_()
+        rt.trace_columns_adjoint(tree, src, NSIDE, out, "f32k", grad_dens=grad)
+        grad2 = torch.zeros_like(grad)
+        rt.trace_columns_adjoint(tree, src, NSIDE, out, "f32k", grad_dens=grad2)
+        same = bool(torch.equal(grad, grad2))
+        del grad2
+        grad_sc = torch.zeros_like(grad)
+        barrier()
+        e0.record(stream)
+        rt.trace_columns_adjoint(tree, src, NSIDE, out, "f32k", grad_dens=grad_sc, path_policy=1)
+        e1.record(stream)
+        barrier()
+        tsc = e0.elapsed_time(e1) / 1e3
+        dmax = float(((grad - grad_sc).abs() / grad_sc.abs().clamp_min(1e-300)).max())
+        extras["adjoint"] = {"ms_per_step": tadj * 1e3, "adjoint_over_forward": tadj / avg_launch_s,
+                             "form": "leaf gather" if sadj["gathered"] else "scatter",
+                             "segments": int(sadj["segments"]), "bitwise_repeatable": same,
+                             "scatter_ms": tsc * 1e3, "scatter_over_forward": tsc / avg_launch_s,
+                             "gather_vs_scatter_max_rel": dmax}
+        del grad, grad_sc
         torch.cuda.empty_cache()
         # ---- fused A_V,eff epilogue: N_H = n(H) + 2 n(H2), a = A_V0 x 125 pc
         AV0_CM2, BOX_CM = 6.29e-22, 125 * 3.0857e18

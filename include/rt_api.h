@@ -82,7 +82,7 @@ typedef struct rt_stats {
     uint64_t exit_fallbacks;  /* F32-Kahan steps whose exit axis needed FP64 */
     uint64_t lookup_fallbacks;/* F32-Kahan steps whose next leaf needed FP64 */
     int32_t status;           /* first device fault (rt_status), RT_OK if none */
-    int32_t reserved;
+    int32_t gathered;         /* 1 if an adjoint call took the leaf gather */
     int64_t fault_ray;        /* ray index (s * n_dirs + q) of that fault, -1 if none */
 } rt_stats;
 
@@ -200,12 +200,24 @@ int rt_trace_paths(const rt_octree* tree, const double* d_src, int64_t n_src, in
  *   d_grad_out: same shape as the forward output; float32 for
  *     RT_MODE_F32_KAHAN, float64 for RT_MODE_FP64.
  *   d_grad_dens: float64 [n_leaves][n_species], ACCUMULATED into (the caller
- *     zeroes it); summation order across rays is not fixed.
- *   path_policy: 0 = automatic (recompute), 1 = recompute the paths while
- *     scattering, 2 = record the paths (rt_record_paths), scatter from the
- *     record and free it (synchronizes `stream`, resets the octree's
- *     statistics).  To reuse a record, call rt_record_paths once and
- *     rt_paths_adjoint / rt_paths_columns many times. */
+ *     zeroes it).
+ *   path_policy:
+ *     0 = automatic.  On a full cube of equal-level leaves with one source per
+ *       leaf, source s in leaf s, all at the same offset inside their leaf
+ *       (leaf centres, for example), every ray of a direction takes the same
+ *       steps and segment lengths, and each leaf's gradient is gathered by one
+ *       thread from per-direction step tables: no atomics, and the same bits
+ *       on every run (F32-Kahan: FP32 products with Kahan compensation, added
+ *       once per leaf in FP64).  The sources are checked on the device; any
+ *       other call (and this one if the check fails) recomputes the paths
+ *       and scatters with FP64 atomics, whose summation order is not fixed.
+ *       The first gather on a handle allocates its step tables (kept by the
+ *       handle and grown when a later call needs more).
+ *     1 = recompute the paths while scattering (FP64 atomics).
+ *     2 = record the paths (rt_record_paths), scatter from the record and
+ *       free it (synchronizes `stream`, resets the octree's statistics).  To
+ *       reuse a record, call rt_record_paths once and rt_paths_adjoint /
+ *       rt_paths_columns many times. */
 int rt_trace_columns_adjoint(const rt_octree* tree, const double* d_src, int64_t n_src,
                              int nside, const void* d_grad_out, int n_species, int mode,
                              double* d_grad_dens, int path_policy, void* stream);
@@ -302,6 +314,10 @@ int rt_octree_info(const rt_octree* tree, int64_t* n_leaves, int* max_level, int
  *   nside: 1, 2, 4 or 8 only; the rest as for rt_trace_columns.
  *   h_stats: NULL, or host memory that receives this call's statistics and
  *     status; then the call synchronizes `stream`.
+ * The launch shape (rt_set_launch) and the ray order are those of
+ * rt_trace_columns.  Each call zeroes the statistics and copies the lookup
+ * entry and the direction table from host tables that are computed once per
+ * nside and never change afterwards.
  * All scratch (work-queue counter, statistics, status word, direction table)
  * lives in one file-scope device array of about 74 KiB that every GPU which
  * loads the library holds until exit.  The first call on a device looks up

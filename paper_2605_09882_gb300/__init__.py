@@ -46,7 +46,7 @@ EPI_AV_EFF, EPI_BETA, EPI_ATTENUATION = 1, 2, 3
 
 class Stats(C.Structure):
     _fields_ = [("rays", C.c_uint64), ("segments", C.c_uint64), ("exit_fallbacks", C.c_uint64),
-                ("lookup_fallbacks", C.c_uint64), ("status", C.c_int32), ("reserved", C.c_int32),
+                ("lookup_fallbacks", C.c_uint64), ("status", C.c_int32), ("gathered", C.c_int32),
                 ("fault_ray", C.c_int64)]
 
 
@@ -393,8 +393,10 @@ class Paths:
 
 
 def trace_columns_adjoint(tree: Octree, src, nside: int, grad_out, mode="f32k", grad_dens=None,
-                          stream=None, path_policy: int = 1):
-    """grad_dens[j,k] += sum over rays of grad_out[s,q,k] * ds(s,q,j) (float64)."""
+                          stream=None, path_policy: int = 0):
+    """grad_dens[j,k] += sum over rays of grad_out[s,q,k] * ds(s,q,j) (float64).
+    path_policy: 0 automatic (the atomic-free leaf gather where the geometry
+    allows it, else the scatter), 1 scatter, 2 scatter from a recorded path."""
     import torch
     m = _mode(mode)
     src = _check_src(src)

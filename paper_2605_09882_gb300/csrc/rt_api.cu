@@ -190,6 +190,7 @@ void rt_destroy_octree(rt_octree* t)
     cudaDeviceSynchronize();
     if (t->table) cudaFree(t->table);
     if (t->st) cudaFree(t->st);
+    if (t->adj_tab) cudaFree(t->adj_tab);
     free(t);
 }
 
@@ -297,6 +298,13 @@ int rt_trace_columns_adjoint(const rt_octree* t, const double* d_src, int64_t n_
     a.gin = d_grad_out;
     a.out = d_grad_dens;
     cudaStream_t s = (cudaStream_t)stream;
+    if (path_policy == 0 && gather_applies(t, a)) {
+        // the leaf gather, with the scatter below as the fallback the device
+        // takes when the sources do not have the gather's layout
+        st = launch_adjoint_gather((rt_octree*)t, a, mode, s);
+        if (st != RT_OK) return st;
+        a.gate = &t->st->gather_off;
+    }
     const int fit = occupancy_adj(mode, n_species, a.t.uniform_level >= 0, g_block);
     if (cudaMemsetAsync(&t->st->queue, 0, sizeof(unsigned long long), s) != cudaSuccess)
         return cuda_error("rt_trace_columns_adjoint: queue reset");
@@ -318,7 +326,7 @@ int rt_get_stats(const rt_octree* t, rt_stats* h_out, void* stream)
     h_out->exit_fallbacks = d.exit_fb;
     h_out->lookup_fallbacks = d.lookup_fb;
     h_out->status = d.status;
-    h_out->reserved = 0;
+    h_out->gathered = d.gathered;
     h_out->fault_ray = d.status ? d.fault_ray : -1;
     return RT_OK;
 }

@@ -293,7 +293,7 @@ int rt_batch_stats(const rt_batch* b, rt_stats* h_out, void* stream)
     h_out->exit_fallbacks = d.exit_fb;
     h_out->lookup_fallbacks = d.lookup_fb;
     h_out->status = d.status;
-    h_out->reserved = 0;
+    h_out->gathered = 0;
     h_out->fault_ray = d.status ? d.fault_ray : -1;
     return RT_OK;
 }

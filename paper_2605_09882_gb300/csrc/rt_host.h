@@ -19,4 +19,8 @@ int sm_count_of(int dev);
 // argument checks and TraceArgs of the single-octree trace entry points
 int prepare_trace(const rt_octree* t, const double* d_src, int64_t n_src, int nside, int S, int mode,
                   TraceArgs& a, const char* who);
+// leaf-gather adjoint (rt_gather.cu): whether the call's shape admits it, and
+// its launch (source check, step tables, gather) on stream s
+bool gather_applies(const rt_octree* t, const TraceArgs& a);
+int launch_adjoint_gather(rt_octree* t, const TraceArgs& a, int mode, cudaStream_t s);
 }  // namespace rt

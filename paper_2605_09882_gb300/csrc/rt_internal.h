@@ -47,8 +47,10 @@ struct DevStats {
     unsigned long long exit_fb;
     unsigned long long lookup_fb;
     int status;
-    int pad;
+    int gather_off;                // adjoint: nonzero when the leaf-gather form does not apply
     long long fault_ray;
+    int gathered;                  // set when a leaf-gather adjoint ran
+    int pad;
 };
 
 struct TraceArgs {
@@ -78,6 +80,9 @@ struct TraceArgs {
     double epi_w[kMaxSpecies];
     double epi_a, epi_gamma;
     const double* epi_coef;
+    // adjoint scatter: runs only if *gate is nonzero (the leaf-gather form did
+    // not apply to this call); NULL: always runs
+    const int* gate;
 };
 
 // Ray order of a trace: direction-major (32 neighbouring sources share a
@@ -104,4 +109,6 @@ struct rt_octree {
     int device;
     int uniform_allowed;     // 0: use the coarse table even for a uniform grid
     int64_t default_cap;
+    void* adj_tab;           // device, owned: step tables of the leaf-gather adjoint (grown on demand)
+    size_t adj_tab_bytes;
 };

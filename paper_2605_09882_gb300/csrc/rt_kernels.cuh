@@ -213,6 +213,7 @@ __global__ void __launch_bounds__(256, (MODE == RT_MODE_F32_KAHAN) ? (UNIFORM ? 
                                                                 : RT_MIN_BLOCKS)
 k_trace(const TraceArgs a)
 {
+    if (KIND == 2 && a.gate && *(volatile const int*)a.gate == 0) return;  // the leaf gather ran instead
     const int lane = threadIdx.x & 31;
     const unsigned long long total = (unsigned long long)(a.layout ? a.n_src : a.n_src_pad) * (unsigned long long)a.nd;
     const long long cap = a.t.step_cap;

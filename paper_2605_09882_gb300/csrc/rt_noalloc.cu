@@ -31,10 +31,16 @@ struct NoAllocScratch {
 // The scratch of every call on this device (about 74 KiB, held until exit).
 static __device__ __align__(256) NoAllocScratch g_noalloc_scratch;
 
-// Host staging copy of the scratch, reused by every call (static storage, so
-// no heap allocation either); the mutex serializes host-side preparation.
-static NoAllocScratch g_stage;
+// Host sources of what every call uploads: one direction table per nside
+// (index log2 nside), each computed on its first use and never changed after,
+// and the possible one-entry lookup tables (entry l: the cube is one uniform
+// level l, entry 22: search all keys).  Static storage, so staging allocates
+// nothing either; the mutex serializes the host-side preparation.
+static DirConst g_dirs_stage[4][kNoAllocMaxDirs];
+static bool g_dirs_ready[4];
 static double g_dirs_host[3 * kNoAllocMaxDirs];
+static const uint64_t kRootEntries[23] = {0,  1,  2,  3,  4,  5,  6,  7,  8,  9,  10, 11,
+                                          12, 13, 14, 15, 16, 17, 18, 19, 20, 21, (uint64_t)kCodeMixed};
 static std::mutex g_noalloc_mu;
 static NoAllocScratch* g_noalloc_ptr[64];  // device address of the array, per device
 
@@ -57,11 +63,15 @@ static NoAllocScratch* noalloc_scratch(int dev, int* status)
     return g_noalloc_ptr[dev];
 }
 
-static void stage_directions(int nside, int nd)
+// The direction constants of nside (1, 2, 4 or 8), computed once.
+static const DirConst* staged_directions(int nside)
 {
+    const int l = nside == 1 ? 0 : nside == 2 ? 1 : nside == 4 ? 2 : 3;
+    if (g_dirs_ready[l]) return g_dirs_stage[l];
+    const int nd = 12 * nside * nside;
     rt_healpix_dirs(nside, g_dirs_host);
     for (int q = 0; q < nd; q++) {
-        DirConst& d = g_stage.dirs[q];
+        DirConst& d = g_dirs_stage[l][q];
         memset(&d, 0, sizeof d);
         for (int b = 0; b < 3; b++) {
             const double v = g_dirs_host[3 * q + b];
@@ -81,6 +91,8 @@ static void stage_directions(int nside, int nd)
                 fabs(d.inv[pa[k]]) == fabs(d.inv[pb[k]]))
                 d.flags |= 1 << (6 + k);
     }
+    g_dirs_ready[l] = true;
+    return g_dirs_stage[l];
 }
 
 }  // namespace rt
@@ -127,13 +139,14 @@ extern "C" int rt_trace_columns_noalloc(const uint64_t* d_keys, const uint8_t* d
 
     const bool full = ext[0] == (1u << kDepth) && ext[1] == (1u << kDepth) && ext[2] == (1u << kDepth);
     const bool uniform = full && max_level <= 10 && n_leaves == (int64_t)(1ll << (3 * max_level));
-    // stage: zeroed statistics, the level-0 lookup entry (O(1) index of a
-    // uniform cube, else a key search over all leaves) and the directions
-    memset(&g_stage.stats, 0, sizeof g_stage.stats);
-    g_stage.root_entry = uniform ? (uint64_t)max_level : (uint64_t)kCodeMixed;
-    stage_directions(nside, nd);
-    const size_t bytes = offsetof(NoAllocScratch, dirs) + sizeof(DirConst) * nd;
-    if (cudaMemcpyAsync(sc, &g_stage, bytes, cudaMemcpyHostToDevice, s) != cudaSuccess)
+    // zeroed statistics, the level-0 lookup entry (O(1) index of a uniform
+    // cube, else a key search over all leaves) and the directions, copied from
+    // host data that never changes once computed
+    if (cudaMemsetAsync(&sc->stats, 0, sizeof(DevStats), s) != cudaSuccess ||
+        cudaMemcpyAsync(&sc->root_entry, &kRootEntries[uniform ? max_level : 22], sizeof(uint64_t),
+                        cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(sc->dirs, staged_directions(nside), sizeof(DirConst) * nd, cudaMemcpyHostToDevice,
+                        s) != cudaSuccess)
         return cuda_error("rt_trace_columns_noalloc: scratch upload");
 
     TraceArgs a;
@@ -157,12 +170,15 @@ extern "C" int rt_trace_columns_noalloc(const uint64_t* d_keys, const uint8_t* d
     a.S = n_species;
     a.out = d_out;
     a.st = &sc->stats;
-    a.batch = 4;
+    // the launch shape and ray order of rt_trace_columns
+    int block, bps, groups;
+    launch_shape(&block, &bps, &groups);
+    a.batch = groups;
+    a.layout = ray_layout(n_src);
     if (n_src > 0) {
-        int sms = 0;
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        const int fit = occupancy_fwd(0, mode, n_species, uniform, 256);
-        if (launch_forward(a, mode, 256, sms * (fit > 0 ? fit : 1), s) != cudaSuccess)
+        const int fit = std::max(1, occupancy_fwd(0, mode, n_species, uniform, block));
+        const int per_sm = bps > 0 ? std::min(bps, fit) : fit;
+        if (launch_forward(a, mode, block, sm_count_of(dev) * per_sm, s) != cudaSuccess)
             return cuda_error("rt_trace_columns_noalloc: launch");
     }
     if (h_stats) {
@@ -175,7 +191,7 @@ extern "C" int rt_trace_columns_noalloc(const uint64_t* d_keys, const uint8_t* d
         h_stats->exit_fallbacks = d.exit_fb;
         h_stats->lookup_fallbacks = d.lookup_fb;
         h_stats->status = d.status;
-        h_stats->reserved = 0;
+        h_stats->gathered = 0;
         h_stats->fault_ray = d.status ? d.fault_ray : -1;
     }
     clear_error();

@@ -392,3 +392,64 @@ def test_corner_crossing_worked_example():
     assert list(leaf) == [0, 4, 7, 35, 56, 60, 63]
     ev = [0.0, 0.1875, 0.125 / a, 0.5625, 0.375 / a, 0.9375, 0.625 / a, 1.3125]
     np.testing.assert_allclose(ds, np.diff(ev), rtol=0, atol=1e-15)
+
+
+# ------------------------------------------------ translation invariance
+
+def _leaf_xyz(keys, lev, idx):
+    sh = (21 - lev[idx].astype(np.int64)).astype(np.uint64)
+    return (synth.deinterleave(keys[idx]) >> sh[:, None]).astype(np.int64)
+
+
+@pytest.mark.parametrize("nside", [1, 2])
+def test_uniform_grid_walk_is_translation_invariant(nside):
+    """On a uniform grid every face-minus-source distance of a leaf-centre
+    source is (k + 1/2) h, the same list for every source, so every exit time
+    and every tie is the same: the steps (leaf offsets) and the segment
+    lengths of two sources agree bit for bit until the nearer one leaves the
+    box.  Offsets along each axis never reverse."""
+    keys, lev = uniform_octree(3)
+    src = synth.leaf_centres(synth.Cloud(keys, lev, np.zeros((keys.shape[0], 1)), (1 << 21,) * 3))
+    rng = np.random.default_rng(31)
+    for m in oracle.healpix(nside):
+        pairs = rng.choice(keys.shape[0], size=(6, 2), replace=False)
+        for a, b in pairs:
+            la, da = oracle.trace_path(keys, lev, src[a], m)
+            lb, db = oracle.trace_path(keys, lev, src[b], m)
+            n = min(la.shape[0], lb.shape[0])
+            oa = _leaf_xyz(keys, lev, la[:n]) - _leaf_xyz(keys, lev, la[:1])
+            ob = _leaf_xyz(keys, lev, lb[:n]) - _leaf_xyz(keys, lev, lb[:1])
+            assert np.array_equal(oa, ob)
+            assert np.array_equal(da[:n].view(np.uint64), db[:n].view(np.uint64))
+            steps = np.diff(oa, axis=0)
+            assert np.all((steps * np.sign(m)[None, :]) >= 0) and np.all(np.abs(steps) <= 1)
+
+
+def test_uniform_grid_adjoint_as_leaf_gather():
+    """The transpose on a uniform grid with one leaf-centre source per leaf,
+    written as a gather over the path of the corner source of each direction:
+    grad[j] = sum_q sum_i [j - o_qi in the box] g[j - o_qi, q] ds_qi, equals the
+    oracle's scatter adjoint."""
+    level = 3
+    keys, lev = uniform_octree(level)
+    n = keys.shape[0]
+    src = synth.leaf_centres(synth.Cloud(keys, lev, np.zeros((n, 1)), (1 << 21,) * 3))
+    dirs = oracle.healpix(1)
+    rng = np.random.default_rng(32)
+    g = rng.random((n, 12, 1))
+    ref = oracle.adjoint(keys, lev, 1, src, dirs, g)
+    xyz = _leaf_xyz(keys, lev, np.arange(n))
+    index = {tuple(v): i for i, v in enumerate(xyz)}
+    N = 1 << level
+    got = np.zeros(n)
+    for q, m in enumerate(dirs):
+        corner = np.where(m < 0, N - 1, 0)
+        c = index[tuple(corner)]
+        path, ds = oracle.trace_path(keys, lev, src[c], m)
+        off = _leaf_xyz(keys, lev, path) - xyz[c]
+        for j in range(n):
+            s = xyz[j][None, :] - off
+            ok = np.all((s >= 0) & (s < N), axis=1)
+            for si, d in zip(s[ok], ds[ok]):
+                got[j] += g[index[tuple(si)], q, 0] * d
+    np.testing.assert_allclose(got, ref[:, 0], rtol=1e-13, atol=0)

@@ -90,6 +90,29 @@ def test_noalloc_matches_handle_entry_point_uniform(rt):
     _compare(rt, cloud.keys, cloud.levels, cloud.dens, synth.leaf_centres(cloud), 1)
 
 
+def test_noalloc_largest_direction_table(rt):
+    """nside 8, the largest table the fixed scratch holds (768 directions), on a
+    small AMR tree."""
+    rng = np.random.default_rng(809)
+    keys, lev, _ = random_octree(rng, 1, 5, 0.35)
+    dens = rng.uniform(0.1, 10.0, size=(keys.shape[0], 2)).astype(np.float32)
+    lo, hi = leaf_boxes(keys, lev)
+    src = np.concatenate([rng.random((40, 3)), 0.5 * (lo + hi)[::9]])
+    _compare(rt, keys, lev, dens, src, 8)
+    _compare(rt, keys, lev, dens, src[:20], 8)  # fewer sources than a warp: source-major ray order
+
+
+def test_noalloc_box_extent_and_fp64_densities(rt):
+    """A box that is not a power of two (extent argument) with FP64 densities."""
+    rng = np.random.default_rng(810)
+    keys, lev, ext = random_octree(rng, 3, 5, 0.3, extent_cells=5)
+    dens = rng.uniform(0.1, 10.0, size=(keys.shape[0], 3))
+    lo, hi = leaf_boxes(keys, lev)
+    box = ext[0] * 2.0 ** -21
+    src = np.concatenate([rng.random((200, 3)) * box, 0.5 * (lo + hi)[::4]])
+    _compare(rt, keys, lev, dens, src, 2, extent=ext)
+
+
 def test_noalloc_rejects_oversized_direction_table(rt):
     import torch
     keys = _dev(np.array([0], dtype=np.uint64))
