@@ -225,18 +225,9 @@ def batched_leg(rt, dev, stream, cache, reps=3):
     p80, 2 FP32 species, leaf-centre sources, Nside 1 or 2) in one launch,
     launch shape from the autotuner."""
     from synth import torchgen
-    g = np.random.default_rng(3)
-    clouds, keep = [], []
-    for i in range(64):
-        b = int(g.choice((16, 24, 32, 48, 64, 96)))
-        r = int(g.integers(0, 4))
-        nside = int(g.choice((1, 2)))
-        k, l, d, n, ext = torchgen.amr_cloud(b, r, 80.0, 1.5, 3000 + i, fracs=(1.0, 0.4), device=dev,
-                                             max_field=192)
-        tree = rt.Octree(k, l, extent=ext)
-        src = torchgen.leaf_centres(k, l)
-        keep.append((k, l))
-        clouds.append((tree, src, nside, d))
+    clouds = []
+    for k, l, d, ext, src, nside in torchgen.batched_clouds(dev):
+        clouds.append((rt.Octree(k, l, extent=ext), src, nside, d))
     batch = rt.Batch(clouds, "f32k")
     best, rate = batch.autotune(cache)
     batch.reset_stats()

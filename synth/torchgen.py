@@ -175,3 +175,23 @@ def mass_weighted_sources(keys, levels, n_tot, n_src: int, seed: int):
     off = torch.minimum((u * span[:, None].to(torch.float64)).to(torch.int64), span[:, None] - 1)
     q = (lo << 32) + off
     return q.to(torch.float64) * 2.0 ** -53
+
+
+def batched_clouds(device="cuda", seed=3, n_clouds=64, base_choices=(16, 24, 32, 48, 64, 96),
+                   max_refine=3, max_field=192):
+    """The 64-cloud batch: per cloud a base size from base_choices (a
+    non-power-of-two base is a box extent inside a power-of-two root), 0 to
+    max_refine levels above the 80th percentile, sigma 1.5, 2 FP32 species
+    (H, H2), leaf-centre sources and HEALPix Nside 1 or 2, all drawn from one
+    seeded stream.  Returns [(keys, levels, dens, extent, src, nside)]."""
+    import numpy as np
+    g = np.random.default_rng(seed)
+    out = []
+    for i in range(n_clouds):
+        b = int(g.choice(base_choices))
+        r = int(g.integers(0, max_refine + 1))
+        nside = int(g.choice((1, 2)))
+        k, l, d, _, ext = amr_cloud(b, r, 80.0, 1.5, 3000 + i, fracs=(1.0, 0.4), device=device,
+                                    max_field=max_field)
+        out.append((k, l, d, ext, leaf_centres(k, l), nside))
+    return out

@@ -43,7 +43,7 @@ def _centres(keys, lev):
 
 def _bound_check(got, ref, mag, rtol):
     d = np.abs(got - ref)
-    lim = rtol * mag + 1e-300
+    lim = rtol * np.abs(mag) + 1e-300
     assert np.all(d <= lim), float((d / np.maximum(mag, 1e-300)).max())
 
 

@@ -1,6 +1,6 @@
 """Full-size parity at 512^3, Nside 1 (the benchmark workload, in the launch
 configuration the benchmark times): the whole trace runs on the GPU; the
-oracle recomputes a random sample of sources one by one.
+oracle recomputes a random sample of 1e5 sources (1.2e6 rays).
 
 Bars: path fingerprints (segment count, hash) of the sampled rays equal the
 oracle's; F32-Kahan columns within 1e-5 relative (+1e-30); FP64-form columns
@@ -14,7 +14,7 @@ import synth
 
 pytestmark = pytest.mark.gpu
 
-N_SAMPLE = 3000
+N_SAMPLE = 100_000  # the paper-scale workload's random oracle subset
 
 
 @pytest.fixture(scope="module")
@@ -39,7 +39,7 @@ def setup():
     assert np.array_equal(src_h, src[torch.from_numpy(idx).cuda()].cpu().numpy())
     want, h_or, n_or = oracle.trace(keys_h, lev_h, dens_h, src_h, oracle.healpix(1))
     yield dict(rt=rt, torch=torch, tree=tree, src=src, dens=dens, idx=idx, want=want, h_or=h_or,
-               n_or=n_or, n=n)
+               n_or=n_or, n=n, keys_h=keys_h, lev_h=lev_h)
     tree.close()
 
 
@@ -81,3 +81,33 @@ def test_fp64_full_trace_sampled(setup):
     assert tree.stats()["status"] == 0
     got = out[torch.from_numpy(setup["idx"]).cuda()].cpu().numpy()
     np.testing.assert_array_equal(got, setup["want"])
+
+
+def test_adjoint_full_size_sparse_seed(setup):
+    """The benchmark's adjoint launch (the leaf gather, F32-Kahan, 4 species)
+    at full size, with a column gradient that is zero except on the 12 rays of
+    2000 random sources: every leaf's gradient is then the oracle's adjoint
+    over those sources alone (g > 0, so the bar is relative), and every other
+    leaf gets exactly zero."""
+    rt, torch = setup["rt"], setup["torch"]
+    tree, n = setup["tree"], setup["n"]
+    rng = np.random.default_rng(57)
+    sel = np.sort(rng.choice(n, size=2000, replace=False))
+    gv = (rng.random((sel.shape[0], 12, 4)) + 0.5).astype(np.float32)
+    g = torch.zeros((n, 12, 4), dtype=torch.float32, device="cuda")
+    g[torch.from_numpy(sel).cuda()] = torch.from_numpy(gv).cuda()
+    tree.reset_stats()
+    grad = rt.trace_columns_adjoint(tree, setup["src"], 1, g, "f32k")
+    st = tree.stats()
+    assert st["status"] == 0 and st["gathered"] == 1, st
+    del g
+    got = grad.cpu().numpy()
+    del grad
+    keys_h, lev_h = setup["keys_h"], setup["lev_h"]
+    src_h = synth.leaf_centres(synth.Cloud(keys_h[sel], lev_h[sel], np.zeros((sel.shape[0], 1)), (1 << 21,) * 3))
+    # two threads: the oracle keeps one gradient copy per thread
+    ref = oracle.adjoint(keys_h, lev_h, 4, src_h, oracle.healpix(1), gv.astype(np.float64), nthreads=2)
+    assert np.all(np.abs(got - ref) <= 1e-5 * ref + 1e-11 * float(gv.max()))
+    assert np.array_equal(got == 0.0, ref == 0.0)
+    touched = ref > 0
+    print("leaves touched", int(touched[:, 0].sum()), "max rel", float((np.abs(got - ref)[touched] / ref[touched]).max()))
