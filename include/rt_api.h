@@ -186,6 +186,34 @@ int rt_trace_epilogue(const rt_octree* tree, const double* d_src, int64_t n_src,
                       const void* d_dens, int n_species, int dens_dtype, int mode,
                       const rt_epilogue* h_epi, double* d_out, void* stream);
 
+/* Forward trace over a chunked contribution grid (Alg. 1: the contribution
+ * grid is traversed one chunk at a time, each ray adds the partial integral
+ * of the part of its path inside the chunk, and sources outside the cloud get
+ * I(p, q) = 0).  The chunks are n_chunks contiguous ranges of about equal size
+ * of the Morton-sorted leaf array; the densities of one chunk at a time are
+ * read, so h_dens may live in HOST memory (page-locked for overlapped copies):
+ * chunk k is copied into one of two device buffers while chunk k - 1 is
+ * traced.  A device pointer is read in place.  Every ray keeps its walk state
+ * and running column sums between chunks (about 48 + 4 n_species bytes of
+ * device scratch per ray, allocated and freed by the call), stops when its
+ * next leaf lies in another chunk and resumes there, and the chunks are swept
+ * in order until every ray has left the domain, so paths and columns are bit
+ * for bit those of rt_trace_columns (which this call reproduces with the
+ * general-octree walk).
+ *   dens: [n_leaves][n_species] of dens_dtype, host or device memory, 16-byte
+ *     aligned.
+ *   d_mask: device uint8 [n_src]; a source with mask 0 is outside the cloud
+ *     and gets zero columns without tracing; NULL traces every source.
+ *   n_chunks: 1 .. n_leaves.
+ *   d_out: as rt_trace_columns.  d_nseg (uint32 [n_src][n_dirs]) and d_hash
+ *     (uint64, as rt_trace_paths) are optional path fingerprints (zero for a
+ *     masked source).
+ * Synchronizes `stream` once per sweep over the chunks and at the end. */
+int rt_trace_columns_chunked(const rt_octree* tree, const double* d_src, int64_t n_src, int nside,
+                             const void* dens, int n_species, int dens_dtype, int mode,
+                             const uint8_t* d_mask, int n_chunks, void* d_out, uint32_t* d_nseg,
+                             uint64_t* d_hash, void* stream);
+
 /* Per-ray path fingerprints: the number of segments and the hash
  * h <- (h XOR leaf) * 0x100000001b3 (h0 = 0xcbf29ce484222325) over the
  * visited leaf indices in walk order, for every ray of the walk that

@@ -15,6 +15,7 @@ import numpy as np
 from . import _build
 
 __all__ = ["Octree", "Batch", "Paths", "trace_epilogue", "build_amr", "healpix_dirs", "trace_columns", "trace_paths", "trace_columns_adjoint",
+           "trace_columns_chunked", "trace_columns_host",
            "Columns", "RTError", "MODE_FP64", "MODE_F32_KAHAN", "set_launch", "lib_path"]
 
 MODE_FP64, MODE_F32_KAHAN = 0, 1
@@ -93,6 +94,7 @@ def _load():
     lib.rt_destroy_paths.restype = None
     lib.rt_trace_columns_host.argtypes = [P, P, i64, P, P, i64, i32, P, i32, i32, i32, P, i64,
                                           C.POINTER(Stats), P]
+    lib.rt_trace_columns_chunked.argtypes = [P, P, i64, i32, P, i32, i32, i32, P, i32, P, P, P, P]
     lib.rt_trace_columns_host_release.argtypes = []
     lib.rt_trace_columns_host_release.restype = None
     return lib
@@ -219,6 +221,41 @@ def trace_columns(tree: Octree, src, nside: int, dens, mode="f32k", out=None, st
                                  F64 if dens.dtype == torch.float64 else F32, m, _dptr(out),
                                  _stream(stream)))
     return out
+
+
+def trace_columns_chunked(tree: Octree, src, nside: int, dens, n_chunks: int, mode="f32k", mask=None,
+                          out=None, paths=False, stream=None):
+    """Columns over a chunked contribution grid: the leaves in n_chunks
+    Morton-range chunks traced one at a time (densities streamed from a CPU
+    tensor, page-locked for overlapped copies, or read in place from a CUDA
+    tensor), with every ray's walk carried between chunks; mask (CUDA uint8
+    or bool [n_src]) selects the sources inside the cloud, the others get zero
+    columns.  Returns the columns, or (columns, nseg, hash) with paths=True."""
+    import torch
+    m = _mode(mode)
+    src = _check_src(src)
+    dens = dens.contiguous()
+    if dens.dim() == 1:
+        dens = dens[:, None]
+    if dens.dtype not in (torch.float32, torch.float64) or dens.shape[0] != tree.n_leaves:
+        raise ValueError("dens must be float32/float64 [n_leaves, S]")
+    S = int(dens.shape[1])
+    nd = 12 * nside * nside
+    odt = torch.float32 if m == MODE_F32_KAHAN else torch.float64
+    if out is None:
+        out = torch.empty((src.shape[0], nd, S), dtype=odt, device=src.device)
+    if mask is not None:
+        mask = mask.to(device=src.device, dtype=torch.uint8).contiguous()
+        if mask.numel() != src.shape[0]:
+            raise ValueError("mask must have one entry per source")
+    nseg = hsh = None
+    if paths:
+        nseg = torch.empty((src.shape[0], nd), dtype=torch.int32, device=src.device)
+        hsh = torch.empty((src.shape[0], nd), dtype=torch.int64, device=src.device)
+    _check(_lib.rt_trace_columns_chunked(tree.handle, _dptr(src), int(src.shape[0]), int(nside), _dptr(dens), S,
+                                         F64 if dens.dtype == torch.float64 else F32, m, _dptr(mask),
+                                         int(n_chunks), _dptr(out), _dptr(nseg), _dptr(hsh), _stream(stream)))
+    return (out, nseg, hsh) if paths else out
 
 
 def trace_columns_host(keys, levels, src, nside: int, dens, mode="f32k", out=None, extent=None,

@@ -15,7 +15,7 @@ LIB = os.path.join(OUT_DIR, "libraytheia_gb300.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC",
               "-Xcompiler", "-ffp-contract=off", "-Xcompiler", "-fno-strict-aliasing"]
-CUDA_SOURCES = ["rt_api.cu", "rt_octree.cu", "rt_forward.cu", "rt_adjoint.cu", "rt_gather.cu", "rt_batched.cu", "rt_paths.cu", "rt_epilogue.cu", "rt_amr.cu", "rt_noalloc.cu", "rt_host_io.cu"]
+CUDA_SOURCES = ["rt_api.cu", "rt_octree.cu", "rt_forward.cu", "rt_adjoint.cu", "rt_gather.cu", "rt_chunked.cu", "rt_batched.cu", "rt_paths.cu", "rt_epilogue.cu", "rt_amr.cu", "rt_noalloc.cu", "rt_host_io.cu"]
 CXX_SOURCES = ["rt_healpix.cpp"]
 
 

@@ -155,6 +155,44 @@ __device__ __forceinline__ bool fixed_source(double x, long long& q)
     return true;
 }
 
+// ------------------------------------------------ resumable walks (chunks)
+
+// Walk state at the top of the step loop: the leaf about to be entered, its
+// box and the time the ray entered it.  It determines the rest of the walk, so
+// a walk stopped there and resumed later visits exactly the leaves and
+// segment lengths of an uninterrupted one.  status: 0 not started, 1 stopped
+// at a leaf outside the chunk being traced, 2 finished.
+struct RayState {
+    uint32_t j;          // leaf about to be entered
+    uint32_t lo[3];      // its lower corner (depth-21 lattice)
+    uint32_t nseg;       // segments so far
+    uint8_t level;       // its level
+    uint8_t status;
+    uint16_t pad;
+    double t;            // FP64 walk: entry time t_in
+    float th, tl;        // F32-Kahan walk: entry time (double-float, depth-21 units)
+    uint64_t hash;       // path fingerprint so far (kept by the caller)
+};
+
+constexpr int kSuspended = -1;  // internal: the walk stopped at a leaf outside the chunk
+
+// Plain walks: no state, never stop early (s is never read).
+struct NoResume {
+    static constexpr bool enabled = false;
+    RayState* s;
+    __device__ __forceinline__ bool inside(long long) const { return true; }
+};
+
+// Walks that trace only the leaves of one contiguous leaf range [j0, j1) (a
+// Morton-range chunk of the linear octree) and stop, saving their state, when
+// the next leaf lies outside it.
+struct ChunkResume {
+    static constexpr bool enabled = true;
+    RayState* s;
+    long long j0, j1;
+    __device__ __forceinline__ bool inside(long long j) const { return j >= j0 && j < j1; }
+};
+
 // ======================================================== FP64 walk (MODE 0)
 
 // Walks one ray in FP64, the operation order of the plain definition:
@@ -163,10 +201,10 @@ __device__ __forceinline__ bool fixed_source(double x, long long& q)
 //   take floor((Q_b + t_out m_b) 2^21) clamped into the current leaf (formed
 //   only when the neighbour is finer than the current leaf; see below).
 // V::seg(j, ds) receives every segment.
-template <bool UNIFORM, class V>
+template <bool UNIFORM, class V, class R = NoResume>
 __device__ __forceinline__ int walk_fp64(const DevTree& t, const DirConst& d,
                                          const double* __restrict__ src, long long cap, V& vis,
-                                         WalkCounters& wc)
+                                         WalkCounters& wc, R* rs = nullptr)
 {
     double Q[3];
     uint32_t c[3];
@@ -188,6 +226,11 @@ __device__ __forceinline__ int walk_fp64(const DevTree& t, const DirConst& d,
         dil = spread10(ci[0]) | (spread10(ci[1]) << 1) | (spread10(ci[2]) << 2);
         j = dil;
         size = 1u << ush;
+    } else if (R::enabled && rs->s->status == 1) {
+        j = rs->s->j;
+#pragma unroll
+        for (int b = 0; b < 3; b++) lo[b] = rs->s->lo[b];
+        size = 1u << (kDepth - rs->s->level);
     } else {
         uint64_t key;
         int level;
@@ -195,9 +238,18 @@ __device__ __forceinline__ int walk_fp64(const DevTree& t, const DirConst& d,
         if (j < 0) return RT_ERR_LOOKUP_MISS;
         leaf_box(key, level, lo, size);
     }
-    double t_in = 0.0;
-    for (long long step = 0;; ++step) {
+    double t_in = (R::enabled && rs->s->status == 1) ? rs->s->t : 0.0;
+    for (long long step = R::enabled ? (long long)rs->s->nseg : 0;; ++step) {
         if (step >= cap) return RT_ERR_STEP_LIMIT;
+        if (R::enabled && !rs->inside(j)) {
+            rs->s->j = (uint32_t)j;
+#pragma unroll
+            for (int b = 0; b < 3; b++) rs->s->lo[b] = lo[b];
+            rs->s->level = (uint8_t)(kDepth - (31 - __clz(size)));
+            rs->s->t = t_in;
+            rs->s->nseg = (uint32_t)step;
+            return kSuspended;
+        }
         if (UNIFORM) {
 #pragma unroll
             for (int b = 0; b < 3; b++) lo[b] = ci[b] << ush;
@@ -790,10 +842,10 @@ __device__ __forceinline__ long long find_leaf(const DevTree& t, const uint32_t 
 // only when that neighbour is finer, at the FP32 position of the non-stepped
 // axes when its certified interval lies inside the leaf found, else at the
 // FP64 position.
-template <int VM, bool QZ, class V>
+template <int VM, bool QZ, class V, class R = NoResume>
 __device__ __forceinline__ int walk_f32k_tree(const DevTree& t, const DirConst* __restrict__ dp,
                                               const double* __restrict__ src, long long cap, V& vis,
-                                              WalkCounters& wc)
+                                              WalkCounters& wc, R* rs = nullptr)
 {
     // The direction's constants (ih, il, m32) are read from the direction
     // table where they are used: one broadcast load per warp, kept out of the
@@ -812,15 +864,37 @@ __device__ __forceinline__ int walk_f32k_tree(const DevTree& t, const DirConst* 
         if (VM & (1 << b)) cE = fmaxf(cE, fabsf(dir_const(&dp->ih[b])) * kEA);
     }
     int level;
-    long long j = find_leaf(t, c, level);
-    if (j < 0) return RT_ERR_LOOKUP_MISS;
-    uint32_t size = 1u << (kDepth - level);
-    uint32_t lo[3];
-#pragma unroll
-    for (int b = 0; b < 3; b++) lo[b] = c[b] & ~(size - 1u);
+    long long j;
+    uint32_t size, lo[3];
     float tih = 0.f, til = 0.f;
-    const uint32_t lim = wc.nseg + (uint32_t)min(cap, (long long)0x7fffffff);  // cap >= 1
+    if (R::enabled && rs->s->status == 1) {
+        j = rs->s->j;
+        level = rs->s->level;
+        size = 1u << (kDepth - level);
+#pragma unroll
+        for (int b = 0; b < 3; b++) lo[b] = rs->s->lo[b];
+        tih = rs->s->th;
+        til = rs->s->tl;
+    } else {
+        j = find_leaf(t, c, level);
+        if (j < 0) return RT_ERR_LOOKUP_MISS;
+        size = 1u << (kDepth - level);
+#pragma unroll
+        for (int b = 0; b < 3; b++) lo[b] = c[b] & ~(size - 1u);
+    }
+    // cap >= 1; a resumed walk counts from the ray's start (wc.nseg holds it)
+    const uint32_t lim = (R::enabled ? 0u : wc.nseg) + (uint32_t)min(cap, (long long)0x7fffffff);
     for (;;) {
+        if (R::enabled && !rs->inside(j)) {
+            rs->s->j = (uint32_t)j;
+#pragma unroll
+            for (int b = 0; b < 3; b++) rs->s->lo[b] = lo[b];
+            rs->s->level = (uint8_t)(kDepth - (31 - __clz(size)));
+            rs->s->th = tih;
+            rs->s->tl = til;
+            rs->s->nseg = wc.nseg;
+            return kSuspended;
+        }
         vis.pre((uint32_t)j);
         float Af[3], th[3], tl[3], ih[3];
 #pragma unroll
@@ -975,6 +1049,40 @@ __device__ __forceinline__ int walk_tree_vm(int vm, const DevTree& t, const DirC
     case 6: return walk_f32k_tree<6, QZ>(t, dp, src, cap, vis, wc);
     default: return walk_f32k_tree<7, QZ>(t, dp, src, cap, vis, wc);
     }
+}
+
+template <bool QZ, class V, class R>
+__device__ __forceinline__ int walk_tree_vm_r(int vm, const DevTree& t, const DirConst* __restrict__ dp,
+                                              const double* __restrict__ src, long long cap, V& vis,
+                                              WalkCounters& wc, R* rs)
+{
+    switch (vm) {
+    case 1: return walk_f32k_tree<1, QZ>(t, dp, src, cap, vis, wc, rs);
+    case 2: return walk_f32k_tree<2, QZ>(t, dp, src, cap, vis, wc, rs);
+    case 3: return walk_f32k_tree<3, QZ>(t, dp, src, cap, vis, wc, rs);
+    case 4: return walk_f32k_tree<4, QZ>(t, dp, src, cap, vis, wc, rs);
+    case 5: return walk_f32k_tree<5, QZ>(t, dp, src, cap, vis, wc, rs);
+    case 6: return walk_f32k_tree<6, QZ>(t, dp, src, cap, vis, wc, rs);
+    default: return walk_f32k_tree<7, QZ>(t, dp, src, cap, vis, wc, rs);
+    }
+}
+
+// General-octree walk of one ray that traces only the leaves of rs's chunk:
+// it starts (status 0) or resumes (status 1) from rs->s and returns
+// kSuspended, with the state saved, at the first leaf outside the chunk.
+// wc.nseg must hold the ray's segment count so far.
+template <int MODE, class V>
+__device__ __forceinline__ int walk_chunk(const DevTree& t, const DirConst* __restrict__ dp,
+                                          const double* __restrict__ src, long long cap, V& vis,
+                                          WalkCounters& wc, ChunkResume* rs)
+{
+    if (MODE == RT_MODE_FP64) {
+        const DirConst d = *dp;
+        return walk_fp64<false>(t, d, src, cap, vis, wc, rs);
+    }
+    const int vm = __ldg(&dp->flags) & 7;
+    return source_on_lattice(src) ? walk_tree_vm_r<true>(vm, t, dp, src, cap, vis, wc, rs)
+                                  : walk_tree_vm_r<false>(vm, t, dp, src, cap, vis, wc, rs);
 }
 
 // Walk of one ray (direction *dp, in global memory) in either arithmetic form.
