@@ -43,7 +43,8 @@ def parse():
     p.add_argument("--no-extras", action="store_true", help="skip FP64 form, adjoint, e2e, CPU baseline")
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
     p.add_argument("--workload", default="uniform512",
-                   choices=["uniform512", "amr128", "batched64", "adjoint_amr64", "dualgrid256", "angular128"],
+                   choices=["uniform512", "amr128", "batched64", "adjoint_amr64", "dualgrid256", "angular128",
+                            "search"],
                    help="uniform512 is the benchmark; the others run one secondary workload alone")
     return p.parse_args()
 
@@ -265,6 +266,43 @@ def adjoint_leg(rt, dev, stream, reps=3):
             "adjoint_over_forward": ta / tf}
 
 
+def search_leg(rt, dev, stream, reps=3):
+    """Key searches (Sec. 2.2.1, the leaf found by a search of the sorted keys):
+    the per-thread binary search against the warp-cooperative search on
+    workloads whose lookups search mixed coarse cells: the 128^3 AMR cloud with
+    its coarse table capped at levels 7, 6 and 5 (and uncapped, level 8, where
+    no lookup searches), and a 128^3 base refined 5 levels (deepest leaf level
+    12, four levels below its table).  F32-Kahan forward, Nside 2, 1M
+    mass-weighted sources each."""
+    import torch
+    from synth import torchgen
+    out = {}
+    for name, nref, caps in (("amr128", 2, (-1, 7, 6, 5)), ("deep128", 5, (-1,))):
+        keys, lev, dens, ntot, ext = torchgen.amr_cloud(128, nref, 90.0, 1.5, 2 if nref == 2 else 7, device=dev)
+        src = torchgen.mass_weighted_sources(keys, lev, ntot, 1_000_000, 102)
+        o = torch.empty((src.shape[0], 48, 4), dtype=torch.float32, device=dev)
+        rows = []
+        for cap in caps:
+            rt.set_table_cap(cap)
+            tree = rt.Octree(keys, lev, extent=ext)
+            rt.set_table_cap(-1)
+            row = {"table_cap": cap, "leaves": int(keys.numel()), "max_level": tree.max_level}
+            for coop in (False, True):
+                tree.set_search(coop)
+                tree.reset_stats()
+                t = timed(lambda: rt.trace_columns(tree, src, 2, dens, "f32k", out=o), stream, reps=reps)
+                st = tree.stats()
+                assert st["status"] == 0, st
+                row["warp" if coop else "thread"] = st["segments"] / (reps + 1) / t
+            rows.append(row)
+            tree.close()
+        out[name] = rows
+        del keys, lev, dens, ntot, src, o
+        torch.cuda.empty_cache()
+    return {"workload": "leaf lookups with key searches: per-thread vs warp-cooperative search (ray-segments/s)",
+            **out}
+
+
 def dualgrid_leg(rt, dev, stream, level=8, reps=1):
     """The paper's dual grid: a uniform source grid (2^level cells per axis,
     lognormal sigma 2, 4 species); the contribution grid is built from it on
@@ -478,6 +516,8 @@ def main():
             r = dualgrid_leg(rt, dev, stream, reps=a.steps)
         elif a.workload == "angular128":
             r = angular_leg(rt, dev, stream, reps=a.steps)
+        elif a.workload == "search":
+            r = search_leg(rt, dev, stream, reps=a.steps)
         else:
             r = adjoint_leg(rt, dev, stream, reps=a.steps)
         if rank == 0:

@@ -74,6 +74,8 @@ def _load():
     lib.rt_set_step_cap.argtypes = [P, i64]
     lib.rt_set_launch.argtypes = [i32, i32, i32]
     lib.rt_set_lookup.argtypes = [P, i32]
+    lib.rt_set_search.argtypes = [P, i32]
+    lib.rt_set_table_cap.argtypes = [i32]
     lib.rt_octree_info.argtypes = [P, C.POINTER(i64), C.POINTER(i32), C.POINTER(i32)]
     lib.rt_last_error.restype = C.c_char_p
     lib.rt_batch_create.argtypes = [P, i32, i32, C.POINTER(P)]
@@ -124,6 +126,11 @@ def healpix_dirs(nside: int) -> np.ndarray:
     out = np.zeros((12 * nside * nside, 3), dtype=np.float64)
     _check(_lib.rt_healpix_dirs(int(nside), out.ctypes.data_as(C.c_void_p)))
     return out
+
+
+def set_table_cap(max_level: int = -1):
+    """Deepest coarse-table level later Octree builds may use (-1: no cap)."""
+    _check(_lib.rt_set_table_cap(int(max_level)))
 
 
 def set_launch(threads_per_block: int = 0, blocks_per_sm: int = 0, groups_per_pop: int = 0):
@@ -183,6 +190,10 @@ class Octree:
 
     def set_lookup(self, use_uniform_index: bool):
         _check(_lib.rt_set_lookup(self._h, 1 if use_uniform_index else 0))
+
+    def set_search(self, warp_cooperative: bool):
+        """Key search in mixed coarse cells: per thread (False) or by the warp."""
+        _check(_lib.rt_set_search(self._h, 1 if warp_cooperative else 0))
 
 
 def _mode(mode) -> int:

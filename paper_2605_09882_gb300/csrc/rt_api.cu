@@ -33,6 +33,9 @@ void clear_error() { g_err.clear(); }
 static int g_block = 256;
 static int g_blocks_per_sm = 0;
 static int g_batch = 4;
+static int g_table_cap = -1;
+
+int table_level_cap() { return g_table_cap; }
 
 struct DeviceInfo {
     int sms = 0;
@@ -213,6 +216,21 @@ int rt_set_step_cap(rt_octree* t, int64_t cap)
 {
     if (!t || cap < 0) return set_error(RT_ERR_ARG, "rt_set_step_cap: bad argument");
     t->dev.step_cap = cap ? cap : t->default_cap;
+    return RT_OK;
+}
+
+int rt_set_search(rt_octree* t, int warp_cooperative)
+{
+    if (!t) return set_error(RT_ERR_ARG, "rt_set_search: null octree");
+    t->dev.search = warp_cooperative ? 1 : 0;
+    return RT_OK;
+}
+
+int rt_set_table_cap(int max_level)
+{
+    if (max_level < -1 || max_level > kMaxTableLevel)
+        return set_error(RT_ERR_ARG, "rt_set_table_cap: max_level must be -1 or in [0, 10]");
+    g_table_cap = max_level;
     return RT_OK;
 }
 

@@ -16,6 +16,8 @@ void launch_shape(int* block, int* blocks_per_sm, int* groups_per_pop);
 // device direction table of nside on device dev (uploaded on first use)
 const DirConst* direction_table(int dev, int nside, int* status);
 int sm_count_of(int dev);
+// deepest coarse-table level rt_build_octree may choose (-1: no cap)
+int table_level_cap();
 // argument checks and TraceArgs of the single-octree trace entry points
 int prepare_trace(const rt_octree* t, const double* d_src, int64_t n_src, int nside, int S, int mode,
                   TraceArgs& a, const char* who);

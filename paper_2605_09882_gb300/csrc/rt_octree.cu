@@ -184,6 +184,8 @@ extern "C" int rt_build_octree(const uint64_t* d_keys, const uint8_t* d_levels, 
             const uint64_t budget = std::max<uint64_t>(1ull << (3 * kBaseTableLevel), 8ull * (uint64_t)n_leaves);
             while (T < std::min(lmax, kMaxTableLevel) && (1ull << (3 * (T + 1))) <= budget) T++;
         }
+        const int cap = table_level_cap();
+        if (cap >= 0) T = std::min(T, cap);
         const uint64_t ncell = 1ull << (3 * T);
         if (cudaMalloc(&t->table, ncell * sizeof(uint64_t)) != cudaSuccess ||
             cudaMalloc(&lvmin, ncell * sizeof(unsigned)) != cudaSuccess ||
@@ -213,6 +215,7 @@ extern "C" int rt_build_octree(const uint64_t* d_keys, const uint8_t* d_levels, 
         d.T = T;
         d.lmax = lmax;
         d.uniform_level = uniform ? lmax : -1;
+        d.search = 0;
         t->uniform_allowed = 1;
         t->default_cap = 3 * (1ll << lmax) + 3;
         d.step_cap = t->default_cap;
