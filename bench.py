@@ -267,12 +267,11 @@ def adjoint_leg(rt, dev, stream, reps=3):
 
 
 def search_leg(rt, dev, stream, reps=3):
-    """Key searches (Sec. 2.2.1, the leaf found by a search of the sorted keys):
-    the per-thread binary search against the warp-cooperative search on
-    workloads whose lookups search mixed coarse cells: the 128^3 AMR cloud with
-    its coarse table capped at levels 7, 6 and 5 (and uncapped, level 8, where
-    no lookup searches), and a 128^3 base refined 5 levels (deepest leaf level
-    12, four levels below its table).  F32-Kahan forward, Nside 2, 1M
+    """Key searches (Sec. 2.2.1, the leaf found by a search of the sorted keys)
+    on workloads whose lookups search mixed coarse cells: the 128^3 AMR cloud
+    with its coarse table capped at levels 7, 6 and 5 (and uncapped, level 8,
+    where no lookup searches), and a 128^3 base refined 5 levels (deepest leaf
+    level 12, four levels below its table).  F32-Kahan forward, Nside 2, 1M
     mass-weighted sources each."""
     import torch
     from synth import torchgen
@@ -287,19 +286,17 @@ def search_leg(rt, dev, stream, reps=3):
             tree = rt.Octree(keys, lev, extent=ext)
             rt.set_table_cap(-1)
             row = {"table_cap": cap, "leaves": int(keys.numel()), "max_level": tree.max_level}
-            for coop in (False, True):
-                tree.set_search(coop)
-                tree.reset_stats()
-                t = timed(lambda: rt.trace_columns(tree, src, 2, dens, "f32k", out=o), stream, reps=reps)
-                st = tree.stats()
-                assert st["status"] == 0, st
-                row["warp" if coop else "thread"] = st["segments"] / (reps + 1) / t
+            tree.reset_stats()
+            t = timed(lambda: rt.trace_columns(tree, src, 2, dens, "f32k", out=o), stream, reps=reps)
+            st = tree.stats()
+            assert st["status"] == 0, st
+            row["value"] = st["segments"] / (reps + 1) / t
             rows.append(row)
             tree.close()
         out[name] = rows
         del keys, lev, dens, ntot, src, o
         torch.cuda.empty_cache()
-    return {"workload": "leaf lookups with key searches: per-thread vs warp-cooperative search (ray-segments/s)",
+    return {"workload": "leaf lookups with key searches, per-thread binary search (ray-segments/s)",
             **out}
 
 

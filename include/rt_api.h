@@ -319,17 +319,10 @@ int rt_set_step_cap(rt_octree* tree, int64_t cap);
  * 0 = default 4).  Applies to later calls in this process. */
 int rt_set_launch(int threads_per_block, int blocks_per_sm, int groups_per_pop);
 
-/* Key search inside a coarse Morton cell that holds leaves of several levels
- * (Sec. 2.2.1: the leaf is found by a search of the sorted key array):
- * 0 (default) a binary search per thread; 1 a warp-cooperative search, in
- * which the lanes of a warp take their pending searches one at a time, each
- * round probing as many evenly spaced keys as there are active lanes and
- * narrowing the range by one ballot.  Both find the same leaf. */
-int rt_set_search(rt_octree* tree, int warp_cooperative);
-
 /* Caps the coarse-table level of later rt_build_octree calls (-1, the
- * default: no cap; 0..10).  A shallower table leaves more lookups to the key
- * search; the results are the same. */
+ * default: no cap; 0..10).  A shallower table leaves more lookups to the
+ * per-thread binary search of the sorted keys inside a coarse cell that holds
+ * leaves of several levels; the results are the same. */
 int rt_set_table_cap(int max_level);
 
 /* Lookup choice: 1 (default) lets a full cube of equal-level leaves use the

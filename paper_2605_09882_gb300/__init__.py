@@ -74,7 +74,6 @@ def _load():
     lib.rt_set_step_cap.argtypes = [P, i64]
     lib.rt_set_launch.argtypes = [i32, i32, i32]
     lib.rt_set_lookup.argtypes = [P, i32]
-    lib.rt_set_search.argtypes = [P, i32]
     lib.rt_set_table_cap.argtypes = [i32]
     lib.rt_octree_info.argtypes = [P, C.POINTER(i64), C.POINTER(i32), C.POINTER(i32)]
     lib.rt_last_error.restype = C.c_char_p
@@ -190,10 +189,6 @@ class Octree:
 
     def set_lookup(self, use_uniform_index: bool):
         _check(_lib.rt_set_lookup(self._h, 1 if use_uniform_index else 0))
-
-    def set_search(self, warp_cooperative: bool):
-        """Key search in mixed coarse cells: per thread (False) or by the warp."""
-        _check(_lib.rt_set_search(self._h, 1 if warp_cooperative else 0))
 
 
 def _mode(mode) -> int:

@@ -219,13 +219,6 @@ int rt_set_step_cap(rt_octree* t, int64_t cap)
     return RT_OK;
 }
 
-int rt_set_search(rt_octree* t, int warp_cooperative)
-{
-    if (!t) return set_error(RT_ERR_ARG, "rt_set_search: null octree");
-    t->dev.search = warp_cooperative ? 1 : 0;
-    return RT_OK;
-}
-
 int rt_set_table_cap(int max_level)
 {
     if (max_level < -1 || max_level > kMaxTableLevel)

@@ -99,48 +99,6 @@ struct WalkCounters {
 
 // ------------------------------------------------------------ leaf lookup
 
-// Warp-cooperative predecessor search (the search of the sorted key array
-// done by a warp with ballots): every active lane with `need` set holds a
-// range [lo, hi) with keys[lo] <= M < keys[hi] (hi = the range end) and gets
-// back in lo the last index whose key is <= M.  The active lanes take the
-// pending searches one at a time: each round all of them probe keys at evenly
-// spaced points of the range, one ballot counts the probes at or below the
-// key, and the range shrinks to the interval between two neighbouring probes,
-// about (active lanes + 1) times smaller.  Control flow is uniform over the
-// active lanes (every value that steers it is broadcast or balloted).
-__device__ __forceinline__ void warp_search(bool need, long long& lo, long long hi, uint64_t M,
-                                            const uint64_t* __restrict__ keys)
-{
-    const unsigned am = __activemask();
-    const int lane = threadIdx.x & 31;
-    const int na = __popc(am);
-    const int r = __popc(am & ((1u << lane) - 1u));  // this lane's rank among the active ones
-    unsigned pend = __ballot_sync(am, need);
-    while (pend) {
-        const int owner = __ffs(pend) - 1;
-        pend &= pend - 1u;
-        long long L = __shfl_sync(am, lo, owner);
-        long long H = __shfl_sync(am, hi, owner);
-        const uint64_t key = __shfl_sync(am, M, owner);
-        while (H - L > 1) {
-            const long long span = H - L;
-            const bool last = span - 1 <= na;  // every candidate gets its own probe
-            const long long p = last ? L + 1 + r : L + ((long long)(r + 1) * span) / (na + 1);
-            const bool le = (p < H) && __ldg(keys + p) <= key;
-            const int k = __popc(__ballot_sync(am, le));
-            if (last) {
-                L += k;
-                H = L + 1;
-            } else {
-                const long long nl = k > 0 ? L + ((long long)k * span) / (na + 1) : L;
-                H = k < na ? L + ((long long)(k + 1) * span) / (na + 1) : H;
-                L = nl;
-            }
-        }
-        if (lane == owner) lo = L;
-    }
-}
-
 // Leaf containing the depth-21 point (cx, cy, cz): coarse Morton table at
 // level T, then an O(1) index for a single-level coarse cell or a binary
 // search of the sorted keys inside a mixed one.  Returns -1 if no leaf
@@ -154,25 +112,6 @@ __device__ __forceinline__ long long lookup_leaf(const DevTree& t, uint32_t cx, 
     const uint64_t e = __ldg(t.table + cell);
     const int code = (int)(e & 63u);
     long long j = (long long)(e >> 6);
-    if (t.search) {
-        const bool need = code == kCodeMixed;
-        long long lo = j, hi = 0;
-        if (need) {
-            const uint64_t ncell = 1ull << (3 * t.T);
-            hi = (cell + 1 < ncell) ? (long long)(__ldg(t.table + cell + 1) >> 6) : t.n;
-        }
-        warp_search(need, lo, hi, M, t.keys);
-        if (code == kCodeHole) return -1;
-        if (code <= kDepth) {
-            if (code > t.T) j += (long long)((M & ((1ull << csh) - 1ull)) >> (3 * (kDepth - code)));
-        } else {
-            j = lo;
-        }
-        key = __ldg(t.keys + j);
-        level = __ldg(t.levels + j);
-        if (M - key >= (1ull << (3 * (kDepth - level)))) return -1;
-        return j;
-    }
     if (code <= kDepth) {
         if (code > t.T) {
             const uint64_t local = (M & ((1ull << csh) - 1ull)) >> (3 * (kDepth - code));
@@ -869,33 +808,6 @@ __device__ __forceinline__ long long find_leaf(const DevTree& t, const uint32_t 
     const uint64_t e = __ldg(t.table + cell);
     const int code = (int)(e & 63u);
     const long long first = (long long)(e >> 6);
-    if (t.search) {
-        const bool need = code == kCodeMixed;
-        long long lo = first, hi = 0;
-        uint64_t M = 0;
-        if (need) {
-            M = interleave3(c[0], c[1], c[2]);
-            const uint64_t ncell = 1ull << (3 * t.T);
-            hi = ((uint64_t)cell + 1 < ncell) ? (long long)(__ldg(t.table + cell + 1) >> 6) : t.n;
-        }
-        warp_search(need, lo, hi, M, t.keys);
-        if (code <= t.T) {
-            level = code;
-            return first;
-        }
-        if (code <= kDepth) {
-            const int sl = kDepth - code;
-            const uint32_t mask = (1u << (code - t.T)) - 1u;
-            level = code;
-            return first + (long long)(spread21((c[0] >> sl) & mask) | (spread21((c[1] >> sl) & mask) << 1) |
-                                       (spread21((c[2] >> sl) & mask) << 2));
-        }
-        if (code == kCodeHole) return -1;
-        const uint64_t key = __ldg(t.keys + lo);
-        level = __ldg(t.levels + lo);
-        if (M - key >= (1ull << (3 * (kDepth - level)))) return -1;
-        return lo;
-    }
     if (code <= t.T) {
         level = code;
         return first;

@@ -26,7 +26,6 @@ struct DevTree {
     int uniform_level;       // >= 0: full cube of leaves all at this level (O(1) index)
     int lmax;
     int64_t step_cap;
-    int search;              // key search in a mixed coarse cell: 0 per thread (binary), 1 warp-cooperative
 };
 
 // Per-direction constants, computed on the host from the HEALPix table.

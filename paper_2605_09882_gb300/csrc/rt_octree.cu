@@ -215,7 +215,6 @@ extern "C" int rt_build_octree(const uint64_t* d_keys, const uint8_t* d_levels, 
         d.T = T;
         d.lmax = lmax;
         d.uniform_level = uniform ? lmax : -1;
-        d.search = 0;
         t->uniform_allowed = 1;
         t->default_cap = 3 * (1ll << lmax) + 3;
         d.step_cap = t->default_cap;
