@@ -260,10 +260,22 @@ def adjoint_leg(rt, dev, stream, reps=3):
     g = torch.rand_like(out)
     grad = torch.zeros((k.numel(), 1), dtype=torch.float64, device=dev)
     ta = timed(lambda: rt.trace_columns_adjoint(tree, src, 2, g, "f32k", grad_dens=grad), stream, reps=reps)
+    # recorded paths: the record's cost, and an adjoint replayed from it
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    paths = rt.Paths(tree, src, 2, "f32k")
+    torch.cuda.synchronize()
+    t_rec = time.perf_counter() - t0
+    t_rep = timed(lambda: paths.adjoint(g, grad_dens=grad), stream, reps=reps)
+    info = paths.info()
+    paths.close()
     tree.close()
+    saved = ta - t_rep
     return {"workload": "64^3 base AMR, 1 level above p85 (%d leaves), 1 species, leaf-centre sources, Nside 2"
                         % k.numel(), "forward_ms": tf * 1e3, "adjoint_ms": ta * 1e3,
-            "adjoint_over_forward": ta / tf}
+            "adjoint_over_forward": ta / tf,
+            "paths": {"record_ms": t_rec * 1e3, "replayed_adjoint_ms": t_rep * 1e3, "record_bytes": info["bytes"],
+                      "adjoints_to_repay_the_record": (t_rec / saved) if saved > 0 else None}}
 
 
 def search_leg(rt, dev, stream, reps=3):
@@ -728,7 +740,7 @@ def main():
         "cpu_baseline": cpu,
         "e2e": e2e,
         "clocks": clk,
-        "gpu_launches": a.steps,
+        "gpu_launches": 2 * a.steps,  # per step: the density check and the trace
     }
     line.update(extras)
     if rank == 0:

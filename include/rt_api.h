@@ -56,7 +56,7 @@ enum rt_status {
     RT_ERR_OVERLAP_OR_GAP = 4,  /* leaves overlap, leave the domain box, or leave a gap */
     RT_ERR_SOURCE_OUTSIDE = 5,  /* a source coordinate is not finite or outside the domain */
     RT_ERR_STEP_LIMIT = 6,      /* a ray reached the step cap (never for a valid octree) */
-    RT_ERR_NONFINITE = 7,       /* reserved */
+    RT_ERR_NONFINITE = 7,       /* a density is NaN, infinite or negative */
     RT_ERR_CUDA = 8,            /* a CUDA runtime call failed; see rt_last_error */
     RT_ERR_OOM = 9,             /* device allocation failed */
     RT_ERR_LOOKUP_MISS = 10     /* a walked position matched no leaf (never for a valid octree) */
@@ -83,7 +83,8 @@ typedef struct rt_stats {
     uint64_t lookup_fallbacks;/* F32-Kahan steps whose next leaf needed FP64 */
     int32_t status;           /* first device fault (rt_status), RT_OK if none */
     int32_t gathered;         /* 1 if an adjoint call took the leaf gather */
-    int64_t fault_ray;        /* ray index (s * n_dirs + q) of that fault, -1 if none */
+    int64_t fault_ray;        /* ray index (s * n_dirs + q) of that fault (for RT_ERR_NONFINITE
+                                 the leaf index), -1 if none */
 } rt_stats;
 
 /* Builds the lookup structures of a leaf-only linear octree (Sec. 2.2.1:
@@ -114,7 +115,13 @@ int rt_healpix_dirs(int nside, double* h_out);
 /* Forward trace (Sec. 2.2, I(p,q) = sum_k f_k r_cell,k, for every source and
  * direction).
  *   d_src: float64 [n_src][3] inside the domain box.
- *   d_dens: [n_leaves][n_species] of dens_dtype; n_species 1..8.
+ *   d_dens: [n_leaves][n_species] of dens_dtype; n_species 1..8.  The
+ *     densities are checked on the device first (one read of the array): a
+ *     NaN, infinite or negative value sets RT_ERR_NONFINITE in the status
+ *     word, with the index of its leaf as the fault position; the columns are
+ *     still computed from the values as given.  rt_trace_epilogue,
+ *     rt_trace_columns_chunked and rt_trace_columns_host (which then returns
+ *     the code) check the same way; a batch does not.
  *   mode: rt_mode.  d_out: [n_src][12 nside^2][n_species], float32 for
  *     RT_MODE_F32_KAHAN, float64 for RT_MODE_FP64; fully written (rays from a
  *     source outside the domain get zeros and set RT_ERR_SOURCE_OUTSIDE).
@@ -409,7 +416,21 @@ void rt_batch_destroy(rt_batch* batch);
  * call with a matching key applies the cached shape without timing.
  * h_best (optional): int[3] = {threads, blocks per SM, groups per pop};
  * h_rate (optional): segments/s of the best shape. */
-int rt_autotune(rt_batch* batch, const char* cache_json, int* h_best, double* h_rate, void* stream);
+int rt_batch_autotune(rt_batch* batch, const char* cache_json, int* h_best, double* h_rate, void* stream);
+
+/* The batch calls in descriptor form (the object API above underneath).
+ * rt_trace_batched traces the n_clouds clouds of h_desc in one persistent
+ * launch replayed as a CUDA graph, enqueued on `stream`: the batch for a
+ * descriptor set is built on its first call (synchronously, an allocation)
+ * and kept, so later calls with the same descriptors (compared byte for
+ * byte, and the same octree builds) and mode only replay it; another
+ * descriptor set replaces it (the old batch is freed after a device
+ * synchronization).  Outputs as rt_trace_columns.
+ * rt_autotune tunes the launch shape on a temporary batch of h_desc (timed on
+ * the legacy default stream) exactly as rt_batch_autotune does, caching in
+ * cache_json (may be NULL), and applies it with rt_set_launch. */
+int rt_trace_batched(const rt_cloud_desc* h_desc, int n_clouds, int mode, void* stream);
+int rt_autotune(const rt_cloud_desc* h_desc, int n_clouds, int mode, const char* cache_json);
 
 /* Message of the last failed call on this host thread ("" if none). */
 const char* rt_last_error(void);

@@ -30,6 +30,7 @@
  * itself prints no column or path values, so no test compares against a
  * printed number.
  */
+#include <float.h>
 #include <math.h>
 #include <pthread.h>
 #include <stdint.h>
@@ -474,6 +475,10 @@ int or_trace(const uint64_t* keys, const uint8_t* levels, int64_t n, const int32
     jb.tree = &t; jb.dens = dens; jb.S = S; jb.src = src; jb.dirs = dirs; jb.nd = nd;
     jb.cap = step_cap(&t); jb.cols = cols; jb.hash = hash; jb.nseg = nseg;
     if (cols && !dens) return OR_ERR_ARG;
+    /* the integrated quantities are number densities: finite and >= 0 */
+    if (cols)
+        for (int64_t e = 0; e < n * S; e++)
+            if (!(dens[e] >= 0.0 && dens[e] <= DBL_MAX)) return OR_ERR_NONFINITE;
     return run_threads(&jb, n_src, nthreads, n);
 }
 

@@ -15,7 +15,7 @@ import numpy as np
 from . import _build
 
 __all__ = ["Octree", "Batch", "Paths", "trace_epilogue", "build_amr", "healpix_dirs", "trace_columns", "trace_paths", "trace_columns_adjoint",
-           "trace_columns_chunked", "trace_columns_host",
+           "trace_columns_chunked", "trace_columns_host", "trace_batched", "autotune",
            "Columns", "RTError", "MODE_FP64", "MODE_F32_KAHAN", "set_launch", "lib_path"]
 
 MODE_FP64, MODE_F32_KAHAN = 0, 1
@@ -83,7 +83,9 @@ def _load():
     lib.rt_batch_reset_stats.argtypes = [P, P]
     lib.rt_batch_destroy.argtypes = [P]
     lib.rt_batch_destroy.restype = None
-    lib.rt_autotune.argtypes = [P, C.c_char_p, C.POINTER(C.c_int * 3), C.POINTER(C.c_double), P]
+    lib.rt_batch_autotune.argtypes = [P, C.c_char_p, C.POINTER(C.c_int * 3), C.POINTER(C.c_double), P]
+    lib.rt_trace_batched.argtypes = [P, i32, i32, P]
+    lib.rt_autotune.argtypes = [P, i32, i32, C.c_char_p]
     lib.rt_trace_epilogue.argtypes = [P, P, i64, i32, P, i32, i32, i32, C.POINTER(Epilogue), P, P]
     lib.rt_build_amr.argtypes = [P, i32, P, i32, i32, i32, C.c_double, C.c_double, i32, P, P, P, i64,
                                  C.POINTER(i64), P]
@@ -454,6 +456,46 @@ def trace_columns_adjoint(tree: Octree, src, nside: int, grad_out, mode="f32k", 
     return grad_dens
 
 
+def _cloud_descs(clouds, mode: int, outputs=None):
+    """Descriptors of (tree, src, nside, dens) clouds, their (new or given)
+    outputs and the tensors that must stay alive while they are used."""
+    import torch
+    odt = torch.float32 if mode == MODE_F32_KAHAN else torch.float64
+    descs = (CloudDesc * len(clouds))()
+    keep, outs = [], []
+    for i, (tree, src, nside, dens) in enumerate(clouds):
+        src = _check_src(src)
+        dens = dens.contiguous()
+        if dens.dim() == 1:
+            dens = dens[:, None]
+        shape = (src.shape[0], 12 * nside * nside, dens.shape[1])
+        out = outputs[i] if outputs is not None else torch.empty(shape, dtype=odt, device=src.device)
+        if out.dtype != odt or tuple(out.shape) != shape or not out.is_contiguous():
+            raise ValueError(f"output {i} has the wrong dtype, shape or layout")
+        keep += [tree, src, dens]
+        outs.append(out)
+        descs[i] = CloudDesc(tree.handle.value, src.data_ptr(), src.shape[0], nside, dens.shape[1],
+                             dens.data_ptr(), F64 if dens.dtype == torch.float64 else F32, 0, out.data_ptr())
+    return descs, outs, keep
+
+
+def trace_batched(clouds, mode="f32k", outputs=None, stream=None):
+    """All clouds [(tree, src, nside, dens)] in one persistent launch replayed
+    as a CUDA graph (rt_trace_batched; the batch is kept and replayed while the
+    same clouds and outputs come back).  Returns the outputs."""
+    m = _mode(mode)
+    descs, outs, _keep = _cloud_descs(clouds, m, outputs)
+    _check(_lib.rt_trace_batched(descs, len(clouds), m, _stream(stream)))
+    return outs
+
+
+def autotune(clouds, mode="f32k", cache_json=None):
+    """Tunes and applies the batched launch shape for these clouds (rt_autotune)."""
+    m = _mode(mode)
+    descs, _outs, _keep = _cloud_descs(clouds, m)
+    _check(_lib.rt_autotune(descs, len(clouds), m, cache_json.encode() if cache_json else None))
+
+
 class Batch:
     """Many clouds traced in one persistent launch, replayed as a CUDA graph.
     clouds: sequence of (tree, src, nside, dens); outputs are allocated here
@@ -497,8 +539,8 @@ class Batch:
         blocks_per_sm, groups_per_pop), segments/s)."""
         best = (C.c_int * 3)()
         rate = C.c_double()
-        _check(_lib.rt_autotune(self._h, cache_json.encode() if cache_json else None, C.byref(best),
-                                C.byref(rate), _stream(stream)))
+        _check(_lib.rt_batch_autotune(self._h, cache_json.encode() if cache_json else None, C.byref(best),
+                                      C.byref(rate), _stream(stream)))
         return tuple(best), rate.value
 
     def close(self):
@@ -518,19 +560,27 @@ try:
 
     class Columns(_torch.autograd.Function):
         """Differentiable columns: forward = trace_columns, backward = the
-        adjoint trace (gradient with respect to the per-leaf densities)."""
+        adjoint trace (gradient with respect to the per-leaf densities).  With
+        paths (a Paths record of the same tree, sources, nside and mode), both
+        are evaluated from the record without walking: the same bits as the
+        walk, worth it when the geometry is reused for several steps."""
 
         @staticmethod
-        def forward(ctx, dens, tree, src, nside, mode="f32k"):
-            ctx.tree, ctx.nside, ctx.mode = tree, nside, mode
+        def forward(ctx, dens, tree, src, nside, mode="f32k", paths=None):
+            ctx.tree, ctx.nside, ctx.mode, ctx.paths = tree, nside, mode, paths
             ctx.save_for_backward(src)
             ctx.dens_dtype = dens.dtype
+            if paths is not None:
+                return paths.columns(dens.detach())
             return trace_columns(tree, src, nside, dens.detach(), mode)
 
         @staticmethod
         def backward(ctx, g):
             (src,) = ctx.saved_tensors
-            gd = trace_columns_adjoint(ctx.tree, src, ctx.nside, g, ctx.mode)
-            return gd.to(ctx.dens_dtype), None, None, None, None
+            if ctx.paths is not None:
+                gd = ctx.paths.adjoint(g)
+            else:
+                gd = trace_columns_adjoint(ctx.tree, src, ctx.nside, g, ctx.mode)
+            return gd.to(ctx.dens_dtype), None, None, None, None, None
 except ImportError:  # pragma: no cover - torch is required for device memory
     Columns = None

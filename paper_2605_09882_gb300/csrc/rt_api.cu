@@ -247,6 +247,14 @@ int rt_trace_columns(const rt_octree* t, const double* d_src, int64_t n_src, int
                      const void* d_dens, int n_species, int dens_dtype, int mode, void* d_out,
                      void* stream)
 {
+    return trace_columns_impl(t, d_src, n_src, nside, d_dens, n_species, dens_dtype, mode, d_out, stream, true);
+}
+
+}  // extern "C"
+
+int rt::trace_columns_impl(const rt_octree* t, const double* d_src, int64_t n_src, int nside, const void* d_dens,
+                           int n_species, int dens_dtype, int mode, void* d_out, void* stream, bool check)
+{
     TraceArgs a;
     int st = prepare_trace(t, d_src, n_src, nside, n_species, mode, a, "rt_trace_columns");
     if (st != RT_OK) return st;
@@ -259,6 +267,10 @@ int rt_trace_columns(const rt_octree* t, const double* d_src, int64_t n_src, int
     a.dens_f64 = dens_dtype == RT_F64;
     a.out = d_out;
     cudaStream_t s = (cudaStream_t)stream;
+    if (check) {
+        const int cs = check_densities(d_dens, t->dev.n, n_species, a.dens_f64, 0, t->st, s);
+        if (cs != RT_OK) return cs;
+    }
     const int fit = occupancy_fwd(0, mode, n_species, a.t.uniform_level >= 0, g_block);
     if (cudaMemsetAsync(&t->st->queue, 0, sizeof(unsigned long long), s) != cudaSuccess)
         return cuda_error("rt_trace_columns: queue reset");
@@ -266,6 +278,8 @@ int rt_trace_columns(const rt_octree* t, const double* d_src, int64_t n_src, int
         return cuda_error("rt_trace_columns: launch");
     return RT_OK;
 }
+
+extern "C" {
 
 int rt_trace_paths(const rt_octree* t, const double* d_src, int64_t n_src, int nside, int mode,
                    uint32_t* d_nseg, uint64_t* d_hash, void* stream)

@@ -6,6 +6,7 @@
 #include <stdio.h>
 #include <stdlib.h>
 
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -390,9 +391,9 @@ static double time_launches(rt_batch* b, cudaStream_t s, int reps)
     return (double)st.segments / (ms * 1e-3);
 }
 
-int rt_autotune(rt_batch* b, const char* cache_json, int* h_best, double* h_rate, void* stream)
+int rt_batch_autotune(rt_batch* b, const char* cache_json, int* h_best, double* h_rate, void* stream)
 {
-    if (!b) return set_error(RT_ERR_ARG, "rt_autotune: null batch");
+    if (!b) return set_error(RT_ERR_ARG, "rt_batch_autotune: null batch");
     cudaStream_t s = (cudaStream_t)stream;
     const std::string key = signature(b);
     int best[3] = {256, 0, 4};
@@ -416,7 +417,7 @@ int rt_autotune(rt_batch* b, const char* cache_json, int* h_best, double* h_rate
         }
         if (rate <= 0.0) {
             rt_set_launch(0, 0, 0);
-            return set_error(RT_ERR_CUDA, "rt_autotune: no configuration ran");
+            return set_error(RT_ERR_CUDA, "rt_batch_autotune: no configuration ran");
         }
         if (cache_json) cache_store(cache_json, key, best, rate);
     }
@@ -424,6 +425,48 @@ int rt_autotune(rt_batch* b, const char* cache_json, int* h_best, double* h_rate
     if (h_best) { h_best[0] = best[0]; h_best[1] = best[1]; h_best[2] = best[2]; }
     if (h_rate) *h_rate = rate;
     return RT_OK;
+}
+
+// The batch of the last rt_trace_batched call, kept for replays while the
+// same descriptors come back (a batch is built synchronously, its graph on
+// the first launch).
+static std::mutex g_tb_mu;
+static rt_batch* g_tb_batch = nullptr;
+static std::vector<rt_cloud_desc> g_tb_desc;
+static std::vector<unsigned long long> g_tb_gen;  // build numbers of the batch's octrees
+static int g_tb_mode = -1;
+
+int rt_trace_batched(const rt_cloud_desc* h_desc, int n_clouds, int mode, void* stream)
+{
+    if (!h_desc || n_clouds < 1) return set_error(RT_ERR_ARG, "rt_trace_batched: bad arguments");
+    std::lock_guard<std::mutex> lk(g_tb_mu);
+    int dev = 0;
+    cudaGetDevice(&dev);
+    bool same = g_tb_batch && g_tb_mode == mode && g_tb_batch->device == dev && (int)g_tb_desc.size() == n_clouds &&
+                memcmp(g_tb_desc.data(), h_desc, sizeof(rt_cloud_desc) * n_clouds) == 0;
+    for (int i = 0; same && i < n_clouds; i++) same = h_desc[i].tree && h_desc[i].tree->gen == g_tb_gen[i];
+    if (!same) {
+        rt_batch_destroy(g_tb_batch);
+        g_tb_batch = nullptr;
+        g_tb_desc.clear();
+        g_tb_gen.clear();
+        const int st = rt_batch_create(h_desc, n_clouds, mode, &g_tb_batch);
+        if (st != RT_OK) return st;
+        g_tb_desc.assign(h_desc, h_desc + n_clouds);
+        for (int i = 0; i < n_clouds; i++) g_tb_gen.push_back(h_desc[i].tree->gen);
+        g_tb_mode = mode;
+    }
+    return rt_batch_launch(g_tb_batch, stream);
+}
+
+int rt_autotune(const rt_cloud_desc* h_desc, int n_clouds, int mode, const char* cache_json)
+{
+    rt_batch* b = nullptr;
+    int st = rt_batch_create(h_desc, n_clouds, mode, &b);
+    if (st != RT_OK) return st;
+    st = rt_batch_autotune(b, cache_json, nullptr, nullptr, nullptr);
+    rt_batch_destroy(b);
+    return st;
 }
 
 }  // extern "C"

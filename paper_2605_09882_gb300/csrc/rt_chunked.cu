@@ -313,6 +313,9 @@ extern "C" int rt_trace_columns_chunked(const rt_octree* t, const double* d_src,
                 cudaStreamWaitEvent(s, copied[b], 0);
                 c.dens = buf[b];
             }
+            if (sweep == 0 &&
+                (st = check_densities(c.dens, j1 - j0, n_species, c.dens_f64, j0, t->st, s)) != RT_OK)
+                break;
             if (cudaMemsetAsync(&t->st->queue, 0, sizeof(unsigned long long), s) != cudaSuccess ||
                 (mode == RT_MODE_FP64 ? launch_pass<RT_MODE_FP64>(c, grid, s)
                                       : launch_pass<RT_MODE_F32_KAHAN>(c, grid, s)) != cudaSuccess) {

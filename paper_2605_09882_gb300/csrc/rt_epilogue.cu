@@ -85,6 +85,8 @@ extern "C" int rt_trace_epilogue(const rt_octree* t, const double* d_src, int64_
     if (h_epi->kind != RT_EPI_ATTENUATION &&
         cudaMemsetAsync(d_out, 0, sizeof(double) * (size_t)n_src, s) != cudaSuccess)
         return cuda_error("rt_trace_epilogue: clear");
+    const int cs = check_densities(d_dens, t->dev.n, n_species, a.dens_f64, 0, t->st, s);
+    if (cs != RT_OK) return cs;
     int block, bps, groups;
     launch_shape(&block, &bps, &groups);
     int dev = 0;

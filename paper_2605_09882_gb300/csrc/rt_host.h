@@ -18,6 +18,14 @@ const DirConst* direction_table(int dev, int nside, int* status);
 int sm_count_of(int dev);
 // deepest coarse-table level rt_build_octree may choose (-1: no cap)
 int table_level_cap();
+// enqueues the density check (RT_ERR_NONFINITE into st for a NaN, infinite or
+// negative value; leaf index base + i / S as the fault position)
+int check_densities(const void* dens, long long n_leaves, int S, int f64, long long base, DevStats* st,
+                    cudaStream_t s);
+// rt_trace_columns with the density check optional (the host-buffer call
+// checks the whole array once, not per source chunk)
+int trace_columns_impl(const rt_octree* t, const double* d_src, int64_t n_src, int nside, const void* d_dens,
+                       int n_species, int dens_dtype, int mode, void* d_out, void* stream, bool check);
 // argument checks and TraceArgs of the single-octree trace entry points
 int prepare_trace(const rt_octree* t, const double* d_src, int64_t n_src, int nside, int S, int mode,
                   TraceArgs& a, const char* who);

@@ -148,6 +148,7 @@ extern "C" int rt_trace_columns_host(const uint64_t* h_keys, const uint8_t* h_le
     }
     if ((st = rt_reset_stats(guard.tree, stream)) != RT_OK) return st;
     if (cudaStreamWaitEvent(cs, w.dens_in, 0) != cudaSuccess) return cuda_error(who);
+    if ((st = check_densities(dens, n_leaves, S, dens_dtype == RT_F64, 0, guard.tree->st, cs)) != RT_OK) return st;
     for (int64_t c = 0; c < n_chunks; c++) {
         const int64_t s0 = c * chunk, n = std::min(chunk, n_src - s0);
         void* slot = out[c & 1];
@@ -156,7 +157,7 @@ extern "C" int rt_trace_columns_host(const uint64_t* h_keys, const uint8_t* h_le
         if (cudaStreamWaitEvent(cs, w.ev[3 * c], 0) != cudaSuccess ||
             (c >= 2 && cudaStreamWaitEvent(cs, w.ev[3 * (c - 2) + 2], 0) != cudaSuccess))
             return cuda_error(who);
-        st = rt_trace_columns(guard.tree, src + 3 * s0, n, nside, dens, S, dens_dtype, mode, slot, stream);
+        st = trace_columns_impl(guard.tree, src + 3 * s0, n, nside, dens, S, dens_dtype, mode, slot, stream, false);
         if (st != RT_OK) return st;
         const size_t bytes = (size_t)n * nd * S * osz;
         if (cudaEventRecord(w.ev[3 * c + 1], cs) != cudaSuccess ||
@@ -171,6 +172,9 @@ extern "C" int rt_trace_columns_host(const uint64_t* h_keys, const uint8_t* h_le
     rt_stats stats;
     if ((st = rt_get_stats(guard.tree, &stats, stream)) != RT_OK) return st;
     if (h_stats) *h_stats = stats;
+    if (stats.status == RT_ERR_NONFINITE)
+        return set_error(stats.status, "rt_trace_columns_host: a density is NaN, infinite or negative (its leaf is "
+                                       "the statistics' fault position)");
     if (stats.status != RT_OK)
         return set_error(stats.status, "rt_trace_columns_host: a ray faulted (its columns are zero; see the statistics)");
     clear_error();

@@ -111,4 +111,5 @@ struct rt_octree {
     int64_t default_cap;
     void* adj_tab;           // device, owned: step tables of the leaf-gather adjoint (grown on demand)
     size_t adj_tab_bytes;
+    unsigned long long gen;  // build number, unique in the process (a reused address is another tree)
 };

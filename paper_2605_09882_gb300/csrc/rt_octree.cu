@@ -3,6 +3,8 @@
 // (Sec. 2.2.1: leaves in compact Morton/level arrays, found by array lookup).
 #include <stdlib.h>
 
+#include <atomic>
+
 #include "rt_device.cuh"
 #include "rt_host.h"
 
@@ -125,6 +127,57 @@ __global__ void k_fill_table(const uint64_t* __restrict__ keys, const uint8_t* _
     }
 }
 
+// Densities are number densities: finite and non-negative.  The first NaN,
+// infinite or negative value found sets RT_ERR_NONFINITE in the status word,
+// with the index of its leaf (base + i / S) as the fault position.
+__global__ void k_check_dens(const void* __restrict__ dens, long long count, int f64, int S, long long base,
+                             DevStats* st)
+{
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long t0 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (!f64) {
+        const float* p = (const float*)dens;
+        const long long nv = count / 4;
+        for (long long i = t0; i < nv; i += stride) {
+            const float4 v = __ldg((const float4*)p + i);
+            const float w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int k = 0; k < 4; k++)
+                if (!(w[k] >= 0.f && w[k] <= 3.402823466e38f)) report_fault(st, RT_ERR_NONFINITE, base + (4 * i + k) / S);
+        }
+        for (long long i = 4 * nv + t0; i < count; i += stride) {
+            const float w = __ldg(p + i);
+            if (!(w >= 0.f && w <= 3.402823466e38f)) report_fault(st, RT_ERR_NONFINITE, base + i / S);
+        }
+    } else {
+        const double* p = (const double*)dens;
+        const long long nv = count / 2;
+        for (long long i = t0; i < nv; i += stride) {
+            const double2 v = __ldg((const double2*)p + i);
+            if (!(v.x >= 0.0 && v.x <= 1.7976931348623157e308)) report_fault(st, RT_ERR_NONFINITE, base + (2 * i) / S);
+            if (!(v.y >= 0.0 && v.y <= 1.7976931348623157e308)) report_fault(st, RT_ERR_NONFINITE, base + (2 * i + 1) / S);
+        }
+        for (long long i = 2 * nv + t0; i < count; i += stride) {
+            const double w = __ldg(p + i);
+            if (!(w >= 0.0 && w <= 1.7976931348623157e308)) report_fault(st, RT_ERR_NONFINITE, base + i / S);
+        }
+    }
+}
+
+int check_densities(const void* dens, long long n_leaves, int S, int f64, long long base, DevStats* st,
+                    cudaStream_t s)
+{
+    const long long count = n_leaves * S;
+    if (count <= 0) return RT_OK;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const long long want = (count / (f64 ? 2 : 4) + 255) / 256 + 1;
+    const int grid = (int)std::min<long long>(want, (long long)sm_count_of(dev) * 8);
+    k_check_dens<<<grid, 256, 0, s>>>(dens, count, f64, S, base, st);
+    if (cudaGetLastError() != cudaSuccess) return cuda_error("density check launch");
+    return RT_OK;
+}
+
 }  // namespace rt
 
 using namespace rt;
@@ -215,6 +268,8 @@ extern "C" int rt_build_octree(const uint64_t* d_keys, const uint8_t* d_levels, 
         d.T = T;
         d.lmax = lmax;
         d.uniform_level = uniform ? lmax : -1;
+        static std::atomic<unsigned long long> builds{0};
+        t->gen = ++builds;
         t->uniform_allowed = 1;
         t->default_cap = 3 * (1ll << lmax) + 3;
         d.step_cap = t->default_cap;

@@ -208,6 +208,14 @@ def test_autograd_function(rt):
     cols = rt.Columns.apply(dens, tree, src, 2, "f32k")
     w = torch.from_numpy(rng.random(cols.shape)).float().cuda()
     (w * cols).sum().backward()
+    # the same step from a path record: the same columns and gradient
+    paths = rt.Paths(tree, src, 2, "f32k")
+    dens2 = dens.detach().clone().requires_grad_(True)
+    cols2 = rt.Columns.apply(dens2, tree, src, 2, "f32k", paths)
+    assert torch.equal(cols2, cols)
+    (w * cols2).sum().backward()
+    torch.testing.assert_close(dens2.grad, dens.grad, rtol=1e-6, atol=0)
+    paths.close()
     g = oracle.adjoint(keys, lev, 2, rng.random((0, 3)), oracle.healpix(2), np.zeros((0, 48, 2)))
     ref = oracle.adjoint(keys, lev, 2, src.cpu().numpy(), oracle.healpix(2),
                          w.cpu().numpy().astype(np.float64))

@@ -84,3 +84,24 @@ def test_autotune_caches_best_shape(clouds, tmp_path):
         assert np.all(np.abs(o - w) <= 1e-5 * np.abs(w) + 1e-30)
     rt.set_launch(0, 0, 0)
     b.close()
+
+
+def test_descriptor_form_calls(clouds, tmp_path):
+    """rt_trace_batched (built on the first call, replayed on the second with
+    the same descriptors) and rt_autotune in descriptor form give the batch
+    object's outputs bit for bit."""
+    import torch
+    rt, cl = clouds
+    spec = [(c["tree"], c["src_d"], c["nside"], c["dens_d"]) for c in cl]
+    b = rt.Batch(spec, "f32k")
+    want = [o.clone() for o in b.launch()]
+    b.close()
+    outs = rt.trace_batched(spec, "f32k")
+    first = [o.clone() for o in outs]
+    for o in outs:
+        o.fill_(float("nan"))
+    rt.trace_batched(spec, "f32k", outputs=outs)  # same descriptors: a replay
+    for w, f, o in zip(want, first, outs):
+        assert torch.equal(w, f) and torch.equal(w, o)
+    rt.autotune(spec, "f32k", str(tmp_path / "tune.json"))
+    rt.set_launch(0, 0, 0)

@@ -316,7 +316,7 @@ def test_linearity():
     n2 = rng.random((keys.shape[0], 1))
     src = rng.random((100, 3))
     dirs = oracle.healpix(2)
-    a, b = 2.5, -0.75
+    a, b = 2.5, 0.75  # densities stay >= 0
     c12, _, _ = oracle.trace(keys, lev, a * n1 + b * n2, src, dirs)
     c1, _, _ = oracle.trace(keys, lev, n1, src, dirs)
     c2, _, _ = oracle.trace(keys, lev, n2, src, dirs)
@@ -453,3 +453,18 @@ def test_uniform_grid_adjoint_as_leaf_gather():
             for si, d in zip(s[ok], ds[ok]):
                 got[j] += g[index[tuple(si)], q, 0] * d
     np.testing.assert_allclose(got, ref[:, 0], rtol=1e-13, atol=0)
+
+
+@pytest.mark.parametrize("bad", [float("nan"), float("inf"), -1.0])
+def test_nonfinite_or_negative_density_is_an_error(bad):
+    """Densities are number densities: a NaN, infinite or negative value is
+    rejected with the non-finite status (the same code the library's density
+    check records)."""
+    keys, lev = uniform_octree(2)
+    dens = np.ones((keys.shape[0], 2))
+    dens[17, 1] = bad
+    with pytest.raises(oracle.OracleError) as e:
+        oracle.trace(keys, lev, dens, np.array([[0.5, 0.5, 0.5]]), oracle.healpix(1))
+    assert e.value.code == oracle.ERR_NONFINITE
+    dens[17, 1] = 0.0  # zero is a valid density
+    oracle.trace(keys, lev, dens, np.array([[0.5, 0.5, 0.5]]), oracle.healpix(1))
