@@ -70,6 +70,7 @@ struct TraceArgs {
     DevStats* st;
     int batch;               // 32-ray groups per queue pop
     int layout;              // ray order: 0 direction-major (sources padded to 32), 1 source-major
+    int dgroup;              // layout 0: directions per group (a power of two dividing nd; <= 1: one)
     // path recording (KIND 3): per 32-ray group, segment k of lane i is entry
     // rec_off[g] + 32 k + i of rec_leaf / rec_ds
     const long long* rec_off;

@@ -228,9 +228,18 @@ k_trace(const TraceArgs a)
             if (g0 >= total) break;
             int q;
             long long s;
-            if (a.layout == 0) {
+            if (a.layout == 0 && a.dgroup <= 1) {
                 q = (int)(g0 / (unsigned long long)a.n_src_pad);
                 s = (long long)(g0 - (unsigned long long)q * a.n_src_pad) + lane;
+                if (s >= a.n_src) continue;
+            } else if (a.layout == 0) {
+                // direction groups: the 32-source block b takes the dgroup
+                // directions of its group in consecutive 32-ray groups, so
+                // the output rows they fill complete whole sectors at once
+                const unsigned long long nb = (unsigned long long)a.n_src_pad >> 5, D = (unsigned)a.dgroup;
+                const unsigned long long g = g0 >> 5, gg = g / (D * nb), r = g - gg * D * nb, b = r / D;
+                q = (int)(gg * D + (r - b * D));
+                s = (long long)(b << 5) + lane;
                 if (s >= a.n_src) continue;
             } else {
                 const unsigned long long r = g0 + lane;
