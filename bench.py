@@ -42,9 +42,10 @@ def parse():
     p.add_argument("--level", type=int, default=LEVEL, help="uniform grid level (9 = 512^3)")
     p.add_argument("--no-extras", action="store_true", help="skip FP64 form, adjoint, e2e, CPU baseline")
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
+    p.add_argument("--amr-base", type=int, default=128, help="base size of the amr128 workload's cloud")
     p.add_argument("--workload", default="uniform512",
                    choices=["uniform512", "amr128", "batched64", "adjoint_amr64", "dualgrid256", "angular128",
-                            "search"],
+                            "search", "adjoint_uniform"],
                    help="uniform512 is the benchmark; the others run one secondary workload alone")
     return p.parse_args()
 
@@ -65,27 +66,44 @@ def peaks():
         return 6800.0, "fallback"
 
 
+# The sources the bench kernel (the forward trace) is compiled and launched
+# from: its device code, its translation unit and the launch code.
+FORWARD_SOURCES = ("paper_2605_09882_gb300/csrc/rt_device.cuh", "paper_2605_09882_gb300/csrc/rt_kernels.cuh",
+                   "paper_2605_09882_gb300/csrc/rt_internal.h", "paper_2605_09882_gb300/csrc/rt_forward.cu",
+                   "paper_2605_09882_gb300/csrc/rt_api.cu", "include/rt_api.h")
+
+
 def kernel_source_sha() -> str:
     h = hashlib.sha256()
-    csrc = os.path.join(ROOT, "paper_2605_09882_gb300", "csrc")
-    for n in sorted(os.listdir(csrc)):
-        with open(os.path.join(csrc, n), "rb") as f:
+    for n in FORWARD_SOURCES:
+        with open(os.path.join(ROOT, n), "rb") as f:
             h.update(n.encode() + f.read())
     return h.hexdigest()[:16]
 
 
-def profiled_traffic():
-    """DRAM bytes per launch of the trace kernel from the committed ncu summary,
-    if it was taken from the current kernel sources (else None)."""
+def kernel_profile():
+    """Per-segment counters of the trace kernel from the committed ncu summary
+    (a 256^3 capture: warp instructions and DRAM bytes per segment), if it was
+    taken from the current kernel sources (else None)."""
     path = os.path.join(ROOT, "profiles", "trace_f32k_uniform512.json")
     try:
         with open(path) as f:
             m = json.load(f)
         if m.get("kernel_source_sha") == kernel_source_sha():
-            return float(m["dram_bytes_per_full_launch"])
+            return {"warp_inst_per_segment": float(m["warp_inst_per_segment"]),
+                    "dram_bytes_per_segment": float(m["dram_bytes_per_segment"])}
     except Exception:
         pass
     return None
+
+
+def profiled_traffic(segments=None):
+    """DRAM bytes of one launch of `segments` segments from the committed
+    summary (scaled per segment), or None when the sources changed since."""
+    p = kernel_profile()
+    if p is None or segments is None:
+        return None
+    return p["dram_bytes_per_segment"] * segments
 
 
 class Clocks:
@@ -132,6 +150,37 @@ class Clocks:
             return None
         return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons),
                 "samples": len(sm)}
+
+
+def issue_roofline(seg_per_launch, launch_s, clk, hbm_gbs, hbm_kind, dev):
+    """The bound of the trace kernel: instruction issue.  Every SM has four
+    schedulers that issue at most one warp instruction per cycle each, so the
+    issue peak is SMs x 4 x the SM clock (the median sampled under load).
+    achieved = segments/s x warp instructions per segment (ncu, 256^3 capture
+    of the same sources).  Beside it: the effective HBM fraction of the 25
+    algorithmic bytes per segment (above 1 because L2 serves the re-reads) and
+    the fraction of HBM bandwidth the measured DRAM traffic uses."""
+    import torch
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    mhz = (clk or {}).get("sm_mhz") or 2070.0
+    issue_peak = sms * 4 * mhz * 1e6
+    prof = kernel_profile()
+    seg_rate = seg_per_launch / launch_s
+    eff = BYTES_PER_SEGMENT * seg_rate / 1e9
+    r = {"bound": "issue", "achieved": None, "peak": issue_peak, "unit": "warp-instructions/s", "frac": None,
+         "traffic": None, "peak_kind": f"derived: {sms} SMs x 4 schedulers x {mhz:.0f} MHz (median under load)",
+         "warp_inst_per_segment": None, "dram_frac": None,
+         "effective_hbm": {"bytes_per_segment": BYTES_PER_SEGMENT, "achieved": eff, "peak": hbm_gbs, "unit": "GB/s",
+                           "frac": eff / hbm_gbs, "peak_kind": hbm_kind},
+         "kernel": "k_trace<fwd, F32K, uniform, S=4>",
+         "profile": "profiles/trace_f32k_uniform512.md (256^3 capture, per segment)"}
+    if prof is not None:
+        r["warp_inst_per_segment"] = prof["warp_inst_per_segment"]
+        r["achieved"] = seg_rate * prof["warp_inst_per_segment"]
+        r["frac"] = r["achieved"] / issue_peak
+        r["traffic"] = prof["dram_bytes_per_segment"] * seg_per_launch
+        r["dram_frac"] = r["traffic"] / launch_s / (hbm_gbs * 1e9)
+    return r
 
 
 # ------------------------------------------------------------------ oracle
@@ -189,13 +238,14 @@ def timed(fn, stream, reps=1):
     return e0.elapsed_time(e1) / 1e3 / reps
 
 
-def amr_leg(rt, dev, stream, check_sources=400, reps=3):
+def amr_leg(rt, dev, stream, check_sources=400, reps=3, base=128):
     """AMR workload: 128^3 base (sigma 1.5), field on 512^3, 2 levels above p90,
     4 FP32 species, 1M mass-weighted sources, Nside 2, F32-Kahan; plus an
-    oracle spot check of a few hundred sources."""
+    oracle spot check of a few hundred sources.  (base: another base size,
+    for profiling a smaller cloud of the same recipe.)"""
     import torch
     from synth import torchgen
-    keys, lev, dens, ntot, ext = torchgen.amr_cloud(128, 2, 90.0, 1.5, 2, device=dev)
+    keys, lev, dens, ntot, ext = torchgen.amr_cloud(base, 2, 90.0, 1.5, 2, device=dev)
     src = torchgen.mass_weighted_sources(keys, lev, ntot, 1_000_000, 102)
     tree = rt.Octree(keys, lev, extent=ext)
     out = torch.empty((src.shape[0], 48, 4), dtype=torch.float32, device=dev)
@@ -204,8 +254,8 @@ def amr_leg(rt, dev, stream, check_sources=400, reps=3):
     st = tree.stats()
     assert st["status"] == 0, st
     segs = st["segments"] / (reps + 1)
-    res = {"workload": "128^3 base AMR (2 levels above p90, %d leaves), 4 FP32 species, 1M mass-weighted "
-                       "sources, Nside 2, F32-Kahan" % keys.numel(),
+    res = {"workload": "%d^3 base AMR (2 levels above p90, %d leaves), 4 FP32 species, 1M mass-weighted "
+                       "sources, Nside 2, F32-Kahan" % (base, keys.numel()),
            "value": segs / t, "unit": "ray-segments/s", "ms_per_step": t * 1e3,
            "segments_per_step": int(segs), "exit_fallbacks_per_step": st["exit_fallbacks"] / 4,
            "lookup_fallbacks_per_step": st["lookup_fallbacks"] / 4}
@@ -276,6 +326,29 @@ def adjoint_leg(rt, dev, stream, reps=3):
             "adjoint_over_forward": ta / tf,
             "paths": {"record_ms": t_rec * 1e3, "replayed_adjoint_ms": t_rep * 1e3, "record_bytes": info["bytes"],
                       "adjoints_to_repay_the_record": (t_rec / saved) if saved > 0 else None}}
+
+
+def adjoint_uniform_leg(rt, dev, stream, level, reps=3):
+    """The paper-scale adjoint alone: 2^level cubed uniform cloud (sigma 2, 4
+    FP32 species), every leaf centre a source, Nside 1: the F32-Kahan forward
+    and the adjoint (the leaf gather) seeded with the forward's columns."""
+    import torch
+    from synth import torchgen
+    keys, lev, dens, _ = torchgen.uniform_cloud(level, 2.0, 5, device=dev)
+    n = keys.numel()
+    src = torchgen.uniform_centres(level, torch.arange(n, device=dev))
+    tree = rt.Octree(keys, lev)
+    out = torch.empty((n, 12, 4), dtype=torch.float32, device=dev)
+    tf = timed(lambda: rt.trace_columns(tree, src, 1, dens, "f32k", out=out), stream, reps=reps)
+    grad = torch.zeros((n, 4), dtype=torch.float64, device=dev)
+    tree.reset_stats()
+    ta = timed(lambda: rt.trace_columns_adjoint(tree, src, 1, out, "f32k", grad_dens=grad), stream, reps=reps)
+    st = tree.stats()
+    tree.close()
+    return {"workload": f"{1 << level}^3 uniform, 4 FP32 species, all leaf centres, Nside 1: forward and adjoint",
+            "forward_ms": tf * 1e3, "adjoint_ms": ta * 1e3, "adjoint_over_forward": ta / tf,
+            "form": "leaf gather" if st["gathered"] else "scatter",
+            "contributions_per_s": st["segments"] / (reps + 1) / ta}
 
 
 def search_leg(rt, dev, stream, reps=3):
@@ -517,7 +590,7 @@ def main():
     stream = torch.cuda.current_stream()
     if a.workload != "uniform512":
         if a.workload == "amr128":
-            r = amr_leg(rt, dev, stream, reps=a.steps)
+            r = amr_leg(rt, dev, stream, reps=a.steps, base=a.amr_base)
         elif a.workload == "batched64":
             r = batched_leg(rt, dev, stream, os.path.join(ROOT, "paper_2605_09882_gb300", "autotune_gb300.json"),
                             reps=a.steps)
@@ -527,6 +600,8 @@ def main():
             r = angular_leg(rt, dev, stream, reps=a.steps)
         elif a.workload == "search":
             r = search_leg(rt, dev, stream, reps=a.steps)
+        elif a.workload == "adjoint_uniform":
+            r = adjoint_uniform_leg(rt, dev, stream, a.level, reps=a.steps)
         else:
             r = adjoint_leg(rt, dev, stream, reps=a.steps)
         if rank == 0:
@@ -578,8 +653,7 @@ def main():
     value = world * seg_per_step * a.steps / (total_ms / 1e3)
     avg_launch_s = float(np.mean(launch_ms)) / 1e3
     peak, peak_kind = peaks()
-    achieved = BYTES_PER_SEGMENT * seg_per_step / avg_launch_s / 1e9
-    traffic = profiled_traffic()
+    roofline = issue_roofline(seg_per_step, avg_launch_s, clk, peak, peak_kind, dev)
 
     extras = {}
     cpu = None
@@ -733,10 +807,7 @@ def main():
                                f"all {n} leaf-centre sources, HEALPix Nside 1 ({n * nd} rays), F32-Kahan columns",
                    "segments_per_step": seg_per_step, "l2": "inputs and output larger than L2 (no flush)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": traffic,
-                     "peak_kind": peak_kind,
-                     "bytes_per_segment": BYTES_PER_SEGMENT, "kernel": "k_trace<fwd, F32K, uniform, S=4>"},
+        "roofline": roofline,
         "cpu_baseline": cpu,
         "e2e": e2e,
         "clocks": clk,
