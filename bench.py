@@ -673,6 +673,21 @@ def main():
         s64 = tree.stats()
         extras["fp64_form"] = {"value": s64["segments"] / t64, "unit": "ray-segments/s",
                                "ms_per_step": t64 * 1e3}
+        # the GPU's FP64 rate, the bound of the FP64 form: a cuBLAS DGEMM
+        # (8192^3, 2 N^3 flops, best of 3), measured here, not assumed
+        A = torch.randn((8192, 8192), dtype=torch.float64, device=dev)
+        B = torch.randn((8192, 8192), dtype=torch.float64, device=dev)
+        torch.matmul(A, B)
+        best = min(timed(lambda: torch.matmul(A, B), stream) for _ in range(3))
+        dgemm = 2 * 8192 ** 3 / best
+        extras["fp64_peak"] = {"dgemm_tflops": dgemm / 1e12,
+                               "what": "cuBLAS FP64 GEMM 8192^3 on this GPU (2 N^3 flops, best of 3)"}
+        # the FP64 walk's FP64 operations per segment at 4 species: ds (1),
+        # the column update (4 DMUL + 4 DADD) and one exit-time update (2)
+        extras["fp64_form"]["fp64_ops_per_segment"] = 11
+        extras["fp64_form"]["fp64_ops_per_s"] = 11 * s64["segments"] / t64
+        extras["fp64_form"]["frac_of_dgemm_fma_rate"] = 11 * s64["segments"] / t64 / (dgemm / 2)
+        del A, B
         # agreement of the two forms on the full output
         mx = torch.zeros(4, dtype=torch.float64, device=dev)
         sm = torch.zeros(4, dtype=torch.float64, device=dev)

@@ -364,12 +364,18 @@ typedef struct {
     double* col;      /* forward: [S] */
     const double* g;  /* adjoint: [S] */
     double* grad;     /* adjoint: [n][S] */
+    int bad;          /* forward: a crossed leaf's density is not a number density */
 } seg_ctx;
 
 static void visit_forward(void* vctx, int64_t j, double ds)
 {
     seg_ctx* x = (seg_ctx*)vctx;
-    for (int k = 0; k < x->S; k++) x->col[k] += x->dens[j * x->S + k] * ds;
+    for (int k = 0; k < x->S; k++) {
+        const double d = x->dens[j * x->S + k];
+        /* the integrated quantities are number densities: finite and >= 0 */
+        if (!(d >= 0.0 && d <= DBL_MAX)) x->bad = 1;
+        x->col[k] += d * ds;
+    }
 }
 
 static void visit_adjoint(void* vctx, int64_t j, double ds)
@@ -396,10 +402,12 @@ static void* run_job(void* arg)
             x.col = col;
             x.g = jb->g ? jb->g + r * jb->S : NULL;
             x.grad = jb->grad;
+            x.bad = 0;
             for (int k = 0; k < jb->S; k++) col[k] = 0.0;
             visit_fn v = jb->g ? visit_adjoint : (jb->cols ? visit_forward : NULL);
             uint64_t ns = 0, h = 0;
             int st = walk(jb->tree, jb->src + 3 * s, jb->dirs + 3 * q, jb->cap, v, &x, &ns, &h);
+            if (st == OR_OK && x.bad) st = OR_ERR_NONFINITE;
             if (st != OR_OK && jb->status == OR_OK) jb->status = st;
             if (st != OR_OK) { ns = 0; h = 0; for (int k = 0; k < jb->S; k++) col[k] = 0.0; }
             if (jb->cols)
@@ -460,7 +468,9 @@ static int run_threads(job_t* base, int64_t n_src, int nthreads, int64_t n_leave
 
 /* Columns I(p,q,k) (Sec. 2.2, Alg. 1's accumulation) for every source and
  * direction; also the per-ray segment count and path hash.  Any output
- * pointer may be NULL.  dens is FP64 [n][S]. */
+ * pointer may be NULL.  dens is FP64 [n][S]: number densities, so a ray that
+ * crosses a leaf whose density is NaN, infinite or negative has no column
+ * (zeroed) and the call returns OR_ERR_NONFINITE. */
 int or_trace(const uint64_t* keys, const uint8_t* levels, int64_t n, const int32_t* extent,
              const double* dens, int S, const double* src, int64_t n_src,
              const double* dirs, int nd, double* cols, uint64_t* hash, uint64_t* nseg,
@@ -475,10 +485,6 @@ int or_trace(const uint64_t* keys, const uint8_t* levels, int64_t n, const int32
     jb.tree = &t; jb.dens = dens; jb.S = S; jb.src = src; jb.dirs = dirs; jb.nd = nd;
     jb.cap = step_cap(&t); jb.cols = cols; jb.hash = hash; jb.nseg = nseg;
     if (cols && !dens) return OR_ERR_ARG;
-    /* the integrated quantities are number densities: finite and >= 0 */
-    if (cols)
-        for (int64_t e = 0; e < n * S; e++)
-            if (!(dens[e] >= 0.0 && dens[e] <= DBL_MAX)) return OR_ERR_NONFINITE;
     return run_threads(&jb, n_src, nthreads, n);
 }
 

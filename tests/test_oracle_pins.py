@@ -457,14 +457,22 @@ def test_uniform_grid_adjoint_as_leaf_gather():
 
 @pytest.mark.parametrize("bad", [float("nan"), float("inf"), -1.0])
 def test_nonfinite_or_negative_density_is_an_error(bad):
-    """Densities are number densities: a NaN, infinite or negative value is
-    rejected with the non-finite status (the same code the library's density
-    check records)."""
+    """Densities are number densities: a ray that crosses a leaf whose density
+    is NaN, infinite or negative has no column, and the trace reports the
+    non-finite status (the code the library's density check records); a ray
+    that does not cross it is unaffected."""
     keys, lev = uniform_octree(2)
     dens = np.ones((keys.shape[0], 2))
     dens[17, 1] = bad
-    with pytest.raises(oracle.OracleError) as e:
-        oracle.trace(keys, lev, dens, np.array([[0.5, 0.5, 0.5]]), oracle.healpix(1))
+    centre = synth.leaf_centres(synth.Cloud(keys, lev, np.zeros((keys.shape[0], 1)), (1 << 21,) * 3))
+    with pytest.raises(oracle.OracleError) as e:  # a source inside the bad leaf crosses it first
+        oracle.trace(keys, lev, dens, centre[17:18], oracle.healpix(1))
     assert e.value.code == oracle.ERR_NONFINITE
+    # +x axis ray from the leaf at the -x face two rows away never enters leaf 17
+    far = np.array([[0.125, 0.875, 0.875]])
+    hit = oracle.trace_path(keys, lev, far[0], [1.0, 0.0, 0.0])[0]
+    assert 17 not in hit
+    cols, _, _ = oracle.trace(keys, lev, dens, far, np.array([[1.0, 0.0, 0.0]]))
+    assert np.all(np.isfinite(cols))
     dens[17, 1] = 0.0  # zero is a valid density
-    oracle.trace(keys, lev, dens, np.array([[0.5, 0.5, 0.5]]), oracle.healpix(1))
+    oracle.trace(keys, lev, dens, centre[17:18], oracle.healpix(1))
