@@ -252,7 +252,11 @@ int rt_trace_paths(const rt_octree* tree, const double* d_src, int64_t n_src, in
  *     2 = record the paths (rt_record_paths), scatter from the record and
  *       free it (synchronizes `stream`, resets the octree's statistics).  To
  *       reuse a record, call rt_record_paths once and rt_paths_adjoint /
- *       rt_paths_columns many times. */
+ *       rt_paths_columns many times.
+ *     3 = deterministic: the leaf gather where it applies (the call then
+ *       synchronizes `stream` to learn whether the sources had its layout),
+ *       otherwise a record, rt_paths_adjoint_ordered over it, and the record
+ *       freed; the same bits on every run. */
 int rt_trace_columns_adjoint(const rt_octree* tree, const double* d_src, int64_t n_src,
                              int nside, const void* d_grad_out, int n_species, int mode,
                              double* d_grad_dens, int path_policy, void* stream);
@@ -305,6 +309,15 @@ int rt_paths_columns(const rt_paths* paths, const void* d_dens, int n_species, i
 /* Adjoint from a record: d_grad_dens[j,k] += sum g[s,q,k] ds (accumulated). */
 int rt_paths_adjoint(const rt_paths* paths, const void* d_grad_out, int n_species,
                      double* d_grad_dens, void* stream);
+
+/* Adjoint from a record like rt_paths_adjoint, but each leaf's terms are
+ * summed by one thread in the record's order (rays as traced, segments in
+ * walk order), FP64 products and sums: the same bits on every run, whatever
+ * the geometry.  The first call sorts the record's slots by leaf (a stable
+ * radix sort; about 8 bytes per slot plus 8 per leaf, kept by the record;
+ * synchronizes `stream`); RT_ERR_ARG for a record of 2^32 or more slots. */
+int rt_paths_adjoint_ordered(rt_paths* paths, const void* d_grad_out, int n_species,
+                             double* d_grad_dens, void* stream);
 
 /* Frees a record (synchronizes the device first).  NULL is ignored. */
 void rt_destroy_paths(rt_paths* paths);

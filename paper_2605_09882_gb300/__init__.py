@@ -93,6 +93,7 @@ def _load():
     lib.rt_paths_info.argtypes = [P, C.POINTER(i64), C.POINTER(i64), C.POINTER(i64)]
     lib.rt_paths_columns.argtypes = [P, P, i32, i32, P, P]
     lib.rt_paths_adjoint.argtypes = [P, P, i32, P, P]
+    lib.rt_paths_adjoint_ordered.argtypes = [P, P, i32, P, P]
     lib.rt_destroy_paths.argtypes = [P]
     lib.rt_destroy_paths.restype = None
     lib.rt_trace_columns_host.argtypes = [P, P, i64, P, P, i64, i32, P, i32, i32, i32, P, i64,
@@ -415,14 +416,18 @@ class Paths:
                                      _dptr(out), _stream(stream)))
         return out
 
-    def adjoint(self, grad_out, grad_dens=None, stream=None):
+    def adjoint(self, grad_out, grad_dens=None, stream=None, ordered=False):
+        """Gradient of the densities from the record (accumulated into
+        grad_dens); ordered=True sums each leaf in the record's order, the same
+        bits on every run (the first such call sorts the record by leaf)."""
         import torch
         gdt = torch.float32 if self.mode == MODE_F32_KAHAN else torch.float64
         grad_out = grad_out.to(gdt).contiguous()
         S = int(grad_out.shape[-1])
         if grad_dens is None:
             grad_dens = torch.zeros((self.tree.n_leaves, S), dtype=torch.float64, device=grad_out.device)
-        _check(_lib.rt_paths_adjoint(self._h, _dptr(grad_out), S, _dptr(grad_dens), _stream(stream)))
+        fn = _lib.rt_paths_adjoint_ordered if ordered else _lib.rt_paths_adjoint
+        _check(fn(self._h, _dptr(grad_out), S, _dptr(grad_dens), _stream(stream)))
         return grad_dens
 
     def close(self):
@@ -441,7 +446,8 @@ def trace_columns_adjoint(tree: Octree, src, nside: int, grad_out, mode="f32k", 
                           stream=None, path_policy: int = 0):
     """grad_dens[j,k] += sum over rays of grad_out[s,q,k] * ds(s,q,j) (float64).
     path_policy: 0 automatic (the atomic-free leaf gather where the geometry
-    allows it, else the scatter), 1 scatter, 2 scatter from a recorded path."""
+    allows it, else the scatter), 1 scatter, 2 scatter from a recorded path,
+    3 deterministic (the leaf gather, else an ordered sum over a record)."""
     import torch
     m = _mode(mode)
     src = _check_src(src)

@@ -325,8 +325,8 @@ int rt_trace_columns_adjoint(const rt_octree* t, const double* d_src, int64_t n_
     TraceArgs a;
     int st = prepare_trace(t, d_src, n_src, nside, n_species, mode, a, "rt_trace_columns_adjoint");
     if (st != RT_OK) return st;
-    if (path_policy < 0 || path_policy > 2)
-        return set_error(RT_ERR_ARG, "rt_trace_columns_adjoint: path_policy must be 0, 1 or 2");
+    if (path_policy < 0 || path_policy > 3)
+        return set_error(RT_ERR_ARG, "rt_trace_columns_adjoint: path_policy must be 0, 1, 2 or 3");
     if (n_src == 0) return RT_OK;
     if (!d_grad_out || !d_grad_dens) return set_error(RT_ERR_ARG, "rt_trace_columns_adjoint: null gradient pointer");
     if (!aligned16(d_grad_out) || !aligned16(d_grad_dens))
@@ -342,6 +342,25 @@ int rt_trace_columns_adjoint(const rt_octree* t, const double* d_src, int64_t n_
     a.gin = d_grad_out;
     a.out = d_grad_dens;
     cudaStream_t s = (cudaStream_t)stream;
+    if (path_policy == 3) {
+        // deterministic: the leaf gather if the sources have its layout, else
+        // the ordered adjoint over a record of the paths
+        if (gather_applies(t, a)) {
+            st = launch_adjoint_gather((rt_octree*)t, a, mode, s);
+            if (st != RT_OK) return st;
+            int off = 1;
+            if (cudaMemcpyAsync(&off, &t->st->gather_off, sizeof off, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+                cudaStreamSynchronize(s) != cudaSuccess)
+                return cuda_error("rt_trace_columns_adjoint: gather flag readback");
+            if (off == 0) return RT_OK;
+        }
+        rt_paths* p = nullptr;
+        st = rt_record_paths(t, d_src, n_src, nside, mode, stream, &p);
+        if (st != RT_OK) return st;
+        st = rt_paths_adjoint_ordered(p, d_grad_out, n_species, d_grad_dens, stream);
+        rt_destroy_paths(p);
+        return st;
+    }
     if (path_policy == 0 && gather_applies(t, a)) {
         // the leaf gather, with the scatter below as the fallback the device
         // takes when the sources do not have the gather's layout

@@ -161,17 +161,94 @@ static int record_occupancy(int mode, bool u, int block)
     return n;
 }
 
+// Sort keys of the record's slots: the leaf of every valid slot, n_leaves (a
+// key past every leaf) for the padding slots of shorter paths; and each
+// slot's ray.
+__global__ void k_slot_keys(const long long* __restrict__ off, const uint32_t* __restrict__ nseg,
+                            const uint32_t* __restrict__ leaf, long long n_groups, long long gq, long long n_src,
+                            int nd, int layout, uint32_t n_leaves, uint32_t* key, uint32_t* slot, uint32_t* slot_ray)
+{
+    const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
+    const int lane = threadIdx.x & 31;
+    for (long long g = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; g < n_groups; g += warps) {
+        long long ray;
+        const bool valid = group_ray(g, lane, gq, n_src, nd, layout, ray);
+        const unsigned ns = valid ? nseg[ray] : 0u;
+        const long long base = off[g] + lane, len = (off[g + 1] - off[g]) >> 5;
+        for (long long k = 0; k < len; k++) {
+            const long long sl = base + 32 * k;
+            key[sl] = k < ns ? leaf[sl] : n_leaves;
+            slot[sl] = (uint32_t)sl;
+            slot_ray[sl] = valid ? (uint32_t)ray : 0u;
+        }
+    }
+}
+
+// First sorted position of every leaf (and of the padding key past them).
+__global__ void k_leaf_start(const uint32_t* __restrict__ skey, long long n_keys, long long n_leaves,
+                             long long* start)
+{
+    for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j <= n_leaves;
+         j += (long long)gridDim.x * blockDim.x) {
+        long long lo = 0, hi = n_keys;
+        while (lo < hi) {
+            const long long mid = (lo + hi) >> 1;
+            if ((long long)skey[mid] < j) lo = mid + 1;
+            else hi = mid;
+        }
+        start[j] = lo;
+    }
+}
+
+// Ordered adjoint: one thread per leaf sums g[ray, k] ds over the leaf's slots
+// in record order (FP64 products of the recorded length and the gradient),
+// then adds the sums to the gradient: the same bits on every run.
+template <int MODE, int SM>
+__global__ void k_paths_ordered(const long long* __restrict__ start, const uint32_t* __restrict__ t_slot,
+                                const uint32_t* __restrict__ slot_ray, const void* __restrict__ ds,
+                                const void* __restrict__ gin, long long n_leaves, int S, double* grad)
+{
+    using T = typename std::conditional<MODE == RT_MODE_FP64, double, float>::type;
+    const T* dsv = (const T*)ds;
+    const T* gv = (const T*)gin;
+    for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < n_leaves;
+         j += (long long)gridDim.x * blockDim.x) {
+        double acc[SM];
+#pragma unroll
+        for (int k = 0; k < SM; k++) acc[k] = 0.0;
+        const long long t1 = start[j + 1];
+        for (long long t = start[j]; t < t1; t++) {
+            const uint32_t sl = __ldg(t_slot + t);
+            const double d = (double)__ldg(dsv + sl);
+            const size_t r = (size_t)__ldg(slot_ray + sl) * S;
+#pragma unroll
+            for (int k = 0; k < SM; k++)
+                if (k < S) acc[k] = __dadd_rn(acc[k], __dmul_rn((double)__ldg(gv + r + k), d));
+        }
+        double* gp = grad + (size_t)j * S;
+#pragma unroll
+        for (int k = 0; k < SM; k++)
+            if (k < S) gp[k] = __dadd_rn(gp[k], acc[k]);
+    }
+}
+
 }  // namespace rt
 
 using namespace rt;
 
 struct rt_paths {
     int device, mode, nd, layout;
-    int64_t n_src, n_src_pad, n_groups, slots, segments;
+    int64_t n_src, n_src_pad, n_groups, slots, segments, n_leaves;
     long long* off;
     uint32_t* nseg;
     uint32_t* leaf;
     void* ds;
+    // leaf-major index of the record (built by the first ordered adjoint):
+    // the record's slots sorted by leaf (stable, so each leaf's slots stay in
+    // record order), each slot's ray, and each leaf's first sorted position
+    uint32_t* t_slot;     // [slots]
+    uint32_t* slot_ray;   // [slots]
+    long long* t_start;   // [n_leaves + 1]
 };
 
 extern "C" {
@@ -184,6 +261,9 @@ void rt_destroy_paths(rt_paths* p)
     cudaFree(p->nseg);
     cudaFree(p->leaf);
     cudaFree(p->ds);
+    cudaFree(p->t_slot);
+    cudaFree(p->slot_ray);
+    cudaFree(p->t_start);
     free(p);
 }
 
@@ -237,6 +317,7 @@ int rt_record_paths(const rt_octree* tree, const double* d_src, int64_t n_src, i
     }
     p->segments = (int64_t)st.segments;
     p->slots = total;
+    p->n_leaves = tree->dev.n;
     if (cudaMalloc(&p->leaf, sizeof(uint32_t) * (size_t)std::max<long long>(1, total)) != cudaSuccess ||
         cudaMalloc(&p->ds, (mode == RT_MODE_FP64 ? 8 : 4) * (size_t)std::max<long long>(1, total)) != cudaSuccess) {
         status = set_error(RT_ERR_OOM, "rt_record_paths: the record does not fit in device memory");
@@ -350,6 +431,87 @@ int rt_paths_adjoint(const rt_paths* p, const void* d_grad_out, int n_species, d
     a.out = d_grad_dens;
     if (launch_paths_kernel<1>(a, p->mode, (cudaStream_t)stream) != cudaSuccess)
         return cuda_error("rt_paths_adjoint: launch");
+    return RT_OK;
+}
+
+// Builds the leaf-major index of a record (once).
+static int build_transpose(rt_paths* p, cudaStream_t s)
+{
+    if (p->t_start) return RT_OK;
+    if (p->slots >= (1ll << 32) || p->n_leaves >= 0xffffffffll)
+        return set_error(RT_ERR_ARG, "rt_paths_adjoint_ordered: the record has 2^32 or more slots");
+    const long long n = std::max<long long>(1, p->slots);
+    uint32_t *key = nullptr, *key2 = nullptr, *slot = nullptr;
+    void* tmp = nullptr;
+    size_t tmp_bytes = 0;
+    int bits = 1;
+    while (bits < 32 && (1ull << bits) <= (unsigned long long)p->n_leaves) bits++;
+    int st = RT_OK;
+    if (cudaMalloc(&key, sizeof(uint32_t) * n) != cudaSuccess || cudaMalloc(&key2, sizeof(uint32_t) * n) != cudaSuccess ||
+        cudaMalloc(&slot, sizeof(uint32_t) * n) != cudaSuccess ||
+        cudaMalloc(&p->t_slot, sizeof(uint32_t) * n) != cudaSuccess ||
+        cudaMalloc(&p->slot_ray, sizeof(uint32_t) * n) != cudaSuccess ||
+        cudaMalloc(&p->t_start, sizeof(long long) * (p->n_leaves + 1)) != cudaSuccess) {
+        st = set_error(RT_ERR_OOM, "rt_paths_adjoint_ordered: the leaf-major index does not fit in device memory");
+    }
+    if (st == RT_OK && p->n_groups > 0) {
+        const int grid = (int)std::min<long long>((p->n_groups + 7) / 8, (long long)sm_count_of(p->device) * 8);
+        k_slot_keys<<<grid, 256, 0, s>>>(p->off, p->nseg, p->leaf, p->n_groups, p->n_src_pad / 32, p->n_src, p->nd,
+                                         p->layout, (uint32_t)p->n_leaves, key, slot, p->slot_ray);
+        cub::DeviceRadixSort::SortPairs(nullptr, tmp_bytes, key, key2, slot, p->t_slot, (long long)p->slots, 0, bits, s);
+        if (cudaMalloc(&tmp, tmp_bytes) != cudaSuccess)
+            st = set_error(RT_ERR_OOM, "rt_paths_adjoint_ordered: sort scratch");
+        else if (cub::DeviceRadixSort::SortPairs(tmp, tmp_bytes, key, key2, slot, p->t_slot, (long long)p->slots, 0, bits,
+                                                 s) != cudaSuccess)
+            st = cuda_error("rt_paths_adjoint_ordered: sort");
+    }
+    if (st == RT_OK) {
+        const int grid = (int)std::min<long long>((p->n_leaves + 256) / 256, 4096);
+        k_leaf_start<<<grid, 256, 0, s>>>(key2, p->slots, p->n_leaves, p->t_start);
+        if (cudaGetLastError() != cudaSuccess) st = cuda_error("rt_paths_adjoint_ordered: index");
+    }
+    cudaStreamSynchronize(s);
+    cudaFree(tmp);
+    cudaFree(key);
+    cudaFree(key2);
+    cudaFree(slot);
+    if (st != RT_OK) {
+        cudaFree(p->t_slot);
+        cudaFree(p->slot_ray);
+        cudaFree(p->t_start);
+        p->t_slot = p->slot_ray = nullptr;
+        p->t_start = nullptr;
+    }
+    return st;
+}
+
+int rt_paths_adjoint_ordered(rt_paths* p, const void* d_grad_out, int n_species, double* d_grad_dens, void* stream)
+{
+    PathArgs a;
+    int st = paths_args(p, n_species, a, "rt_paths_adjoint_ordered");
+    if (st != RT_OK) return st;
+    if (p->n_src == 0) return RT_OK;
+    if (!d_grad_out || !d_grad_dens)
+        return set_error(RT_ERR_ARG, "rt_paths_adjoint_ordered: null gradient pointer");
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((st = build_transpose(p, s)) != RT_OK) return st;
+    const int grid = (int)std::min<long long>((p->n_leaves + 255) / 256, (long long)sm_count_of(p->device) * 16);
+#define RT_ORD_GO(M, SMV)                                                                                          \
+    k_paths_ordered<M, SMV><<<grid, 256, 0, s>>>(p->t_start, p->t_slot, p->slot_ray, p->ds, d_grad_out, p->n_leaves, \
+                                                 n_species, d_grad_dens)
+    if (p->mode == RT_MODE_FP64) {
+        if (n_species <= 1) RT_ORD_GO(RT_MODE_FP64, 1);
+        else if (n_species <= 2) RT_ORD_GO(RT_MODE_FP64, 2);
+        else if (n_species <= 4) RT_ORD_GO(RT_MODE_FP64, 4);
+        else RT_ORD_GO(RT_MODE_FP64, 8);
+    } else {
+        if (n_species <= 1) RT_ORD_GO(RT_MODE_F32_KAHAN, 1);
+        else if (n_species <= 2) RT_ORD_GO(RT_MODE_F32_KAHAN, 2);
+        else if (n_species <= 4) RT_ORD_GO(RT_MODE_F32_KAHAN, 4);
+        else RT_ORD_GO(RT_MODE_F32_KAHAN, 8);
+    }
+#undef RT_ORD_GO
+    if (cudaGetLastError() != cudaSuccess) return cuda_error("rt_paths_adjoint_ordered: launch");
     return RT_OK;
 }
 

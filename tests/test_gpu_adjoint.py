@@ -106,12 +106,14 @@ def test_uniform_grid_adjoint_matches_oracle(rt, S):
     tree.close()
 
 
-@pytest.mark.parametrize("policy", [0, 2])
+@pytest.mark.parametrize("policy", [0, 2, 3])
 def test_c4_adjoint_matches_oracle(rt, policy):
     """The differentiable workload itself (64^3 base refined once above p85,
     537,398 leaves, one species, Nside 2) on 3000 random leaf-centre sources,
     the same on both sides, with gradients of both signs; recomputed paths
-    (policy 0, the scatter on a general octree) and a recorded path (policy 2)."""
+    (policy 0, the scatter on a general octree), a recorded path (policy 2)
+    and the deterministic form (policy 3: an ordered sum over a record, the
+    same bits on a second call)."""
     cloud, src_all, nside = synth.workload_amr64_grad()
     rng = np.random.default_rng(44)
     src = src_all[np.sort(rng.choice(src_all.shape[0], size=3000, replace=False))]
@@ -128,6 +130,12 @@ def test_c4_adjoint_matches_oracle(rt, policy):
     gk = rt.trace_columns_adjoint(tree, _dev(src), nside, _dev(g.astype(np.float32)), "f32k",
                                   path_policy=policy).cpu().numpy()
     _check_f32k(gk, refk, magk, g32)
+    if policy == 3:
+        again = rt.trace_columns_adjoint(tree, _dev(src), nside, _dev(g.astype(np.float32)), "f32k",
+                                         path_policy=3).cpu().numpy()
+        assert np.array_equal(gk.view(np.uint64), again.view(np.uint64))
+        gd2 = rt.trace_columns_adjoint(tree, _dev(src), nside, _dev(g), "fp64", path_policy=3).cpu().numpy()
+        assert np.array_equal(gd.view(np.uint64), gd2.view(np.uint64))
     touched = mag[:, 0] > 0
     rel = np.abs(gk - refk)[touched, 0] / mag[touched, 0]
     print("policy", policy, "leaves touched", int(touched.sum()), "f32k max rel (of mag)", float(rel.max()))

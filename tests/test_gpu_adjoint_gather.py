@@ -71,6 +71,8 @@ def test_gather_matches_oracle(rt, level, S, nside):
     _bound_check(gd, ref, mag, 1e-12)
     again, _ = _run(rt, tree, src, nside, _dev(g), "fp64")
     assert np.array_equal(gd.view(np.uint64), again.view(np.uint64))
+    det, st_det = _run(rt, tree, src, nside, _dev(g), "fp64", policy=3)  # deterministic: the gather
+    assert st_det["gathered"] == 1 and np.array_equal(gd.view(np.uint64), det.view(np.uint64))
     sc, st_sc = _run(rt, tree, src, nside, _dev(g), "fp64", policy=1)
     assert st_sc["gathered"] == 0 and st_sc["segments"] == st["segments"] and st_sc["rays"] == st["rays"]
     _bound_check(gd, sc, mag, 2e-12)
@@ -133,6 +135,11 @@ def test_gather_falls_back_to_scatter(rt, how):
     gd, st = _run(rt, tree, _dev(src_h), 1, _dev(g), "fp64")
     assert st["gathered"] == 0
     _bound_check(gd, ref, mag, 1e-12)
+    # deterministic: the ordered sum over a record, the same bits twice
+    d1, _ = _run(rt, tree, _dev(src_h), 1, _dev(g), "fp64", policy=3)
+    d2, _ = _run(rt, tree, _dev(src_h), 1, _dev(g), "fp64", policy=3)
+    _bound_check(d1, ref, mag, 1e-12)
+    assert np.array_equal(d1.view(np.uint64), d2.view(np.uint64))
     tree.close()
 
 
