@@ -267,6 +267,15 @@ def amr_leg(rt, dev, stream, check_sources=400, reps=3, base=128):
     got = out[idx].double().cpu().numpy()
     err = np.abs(got - want) / np.maximum(np.abs(want), 1e-300)
     res["parity_sample"] = {"n_src": int(idx.numel()), "max_rel": float(err.max())}
+    # Alg. 1's chunked contribution grid: 8 Morton-range chunks, densities
+    # streamed from page-locked host memory, rays carried between chunks
+    d_host = dens.cpu().pin_memory()
+    tree.reset_stats()
+    tc = timed(lambda: rt.trace_columns_chunked(tree, src, 2, d_host, 8, "f32k", out=out), stream, reps=1)
+    stc = tree.stats()
+    assert stc["status"] == 0, stc
+    res["chunked8_host"] = {"value": stc["segments"] / 2 / tc, "unit": "ray-segments/s", "ms_per_step": tc * 1e3,
+                            "what": "8 chunks, densities streamed from page-locked host memory"}
     tree.close()
     return res
 

@@ -19,6 +19,8 @@
 // exactly those of the unchunked trace, and so are the paths and the columns
 // (bit for bit).  A ray may leave a chunk and come back to it later, so the
 // chunks are swept in order until every ray has finished.
+#include <vector>
+
 #include "rt_host.h"
 #include "rt_kernels.cuh"
 
@@ -41,8 +43,28 @@ struct ChunkArgs {
     uint64_t* hash;
     DevStats* st;
     unsigned long long* done;  // rays finished
+    // per-chunk queues of the rays waiting at a leaf of that chunk: the pass of
+    // chunk c walks queue c (the first pass of all walks every ray); a ray
+    // that stops appends itself to the queue of its next leaf's chunk
+    uint32_t* queues;          // [n_chunks][n_rays]
+    unsigned long long* qcount;  // [n_chunks]
+    const long long* bounds;   // [n_chunks + 1] first leaf of every chunk
+    long long n_rays;
+    int n_chunks, chunk, fresh;
     int batch, layout;
 };
+
+// Chunk of leaf j: the last c with bounds[c] <= j.
+__device__ __forceinline__ int chunk_of(const long long* __restrict__ bounds, int n_chunks, long long j)
+{
+    int lo = 0, hi = n_chunks;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(bounds + mid) <= j) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
 
 // Column sums that continue from the ray's running values, reading the
 // densities of chunk leaves (index j - j0 in the chunk buffer), and the path
@@ -85,12 +107,17 @@ struct ChunkCols {
 // One pass: every unfinished ray whose walk is at a leaf of the chunk (or that
 // has not started) walks until its next leaf lies outside the chunk or the ray
 // leaves the domain.
+#ifndef RT_MIN_BLOCKS_CHUNK
+#define RT_MIN_BLOCKS_CHUNK 3
+#endif
 template <int MODE, int SM>
-__global__ void __launch_bounds__(256) k_chunk_pass(const ChunkArgs a)
+__global__ void __launch_bounds__(256, RT_MIN_BLOCKS_CHUNK) k_chunk_pass(const ChunkArgs a)
 {
     using T = typename std::conditional<MODE == RT_MODE_FP64, double, float>::type;
     const int lane = threadIdx.x & 31;
-    const unsigned long long total = (unsigned long long)(a.layout ? a.n_src : a.n_src_pad) * (unsigned long long)a.nd;
+    const unsigned long long total = a.fresh ? (unsigned long long)(a.layout ? a.n_src : a.n_src_pad) * (unsigned long long)a.nd
+                                             : *(volatile unsigned long long*)(a.qcount + a.chunk);
+    const uint32_t* myq = a.queues + (size_t)a.chunk * (size_t)a.n_rays;
     unsigned long long n_rays = 0, n_segs = 0, n_efb = 0, n_lfb = 0, n_done = 0;
     for (;;) {
         unsigned long long base = 0;
@@ -102,7 +129,12 @@ __global__ void __launch_bounds__(256) k_chunk_pass(const ChunkArgs a)
             if (g0 >= total) break;
             int q;
             long long s;
-            if (a.layout == 0) {
+            if (!a.fresh) {
+                if (g0 + lane >= total) continue;
+                const long long r = (long long)__ldg(myq + g0 + lane);
+                s = r / a.nd;
+                q = (int)(r - s * a.nd);
+            } else if (a.layout == 0) {
                 q = (int)(g0 / (unsigned long long)a.n_src_pad);
                 s = (long long)(g0 - (unsigned long long)q * a.n_src_pad) + lane;
                 if (s >= a.n_src) continue;
@@ -152,6 +184,16 @@ __global__ void __launch_bounds__(256) k_chunk_pass(const ChunkArgs a)
             if (st == kSuspended) {
                 rs.status = 1;
                 rs.hash = v.h;
+                // join the queue of the next leaf's chunk (one atomic per
+                // chunk per warp)
+                const int cn = chunk_of(a.bounds, a.n_chunks, (long long)rs.j);
+                const unsigned am = __activemask();
+                const unsigned peers = __match_any_sync(am, cn);
+                const int leader = __ffs(peers) - 1;
+                unsigned long long slot = 0;
+                if (lane == leader) slot = atomicAdd(a.qcount + cn, (unsigned long long)__popc(peers));
+                slot = __shfl_sync(peers, slot, leader) + __popc(peers & ((1u << lane) - 1u));
+                a.queues[(size_t)cn * (size_t)a.n_rays + slot] = (uint32_t)ray;
 #pragma unroll
                 for (int k = 0; k < SM; k++) {
                     if (k < a.S) {
@@ -247,15 +289,25 @@ extern "C" int rt_trace_columns_chunked(const rt_octree* t, const double* d_src,
     const size_t rs_bytes = ((size_t)n_rays * sizeof(RayState) + 255) / 256 * 256;
     const size_t cmp_bytes = mode == RT_MODE_FP64 ? 0 : ((size_t)n_rays * n_species * 4 + 255) / 256 * 256;
     const size_t buf_bytes = on_device ? 0 : ((size_t)max_chunk * n_species * dsz + 255) / 256 * 256;
+    if (n_rays >= (1ll << 32))
+        return set_error(RT_ERR_ARG, "rt_trace_columns_chunked: 2^32 or more rays in one call");
+    const size_t head_bytes = ((size_t)(2 * n_chunks + 2) * 8 + 255) / 256 * 256;  // done, counts, bounds
+    const size_t q_bytes = ((size_t)n_chunks * n_rays * 4 + 255) / 256 * 256;
     char* scratch = nullptr;
-    if (cudaMalloc(&scratch, 256 + rs_bytes + cmp_bytes + 2 * buf_bytes) != cudaSuccess) {
+    if (cudaMalloc(&scratch, head_bytes + rs_bytes + cmp_bytes + q_bytes + 2 * buf_bytes) != cudaSuccess) {
         cudaGetLastError();
         return set_error(RT_ERR_OOM, "rt_trace_columns_chunked: the ray states do not fit in device memory");
     }
     unsigned long long* done = (unsigned long long*)scratch;
-    RayState* rs = (RayState*)(scratch + 256);
-    float* cmp = mode == RT_MODE_FP64 ? nullptr : (float*)(scratch + 256 + rs_bytes);
-    char* buf[2] = {scratch + 256 + rs_bytes + cmp_bytes, scratch + 256 + rs_bytes + cmp_bytes + buf_bytes};
+    unsigned long long* qcount = done + 1;
+    long long* bounds = (long long*)(qcount + n_chunks);
+    RayState* rs = (RayState*)(scratch + head_bytes);
+    float* cmp = mode == RT_MODE_FP64 ? nullptr : (float*)(scratch + head_bytes + rs_bytes);
+    uint32_t* queues = (uint32_t*)(scratch + head_bytes + rs_bytes + cmp_bytes);
+    char* buf[2] = {scratch + head_bytes + rs_bytes + cmp_bytes + q_bytes,
+                    scratch + head_bytes + rs_bytes + cmp_bytes + q_bytes + buf_bytes};
+    std::vector<long long> h_bounds(n_chunks + 1);
+    for (int c = 0; c <= n_chunks; c++) h_bounds[c] = n * c / n_chunks;
     cudaStream_t cs = nullptr;
     cudaEvent_t copied[2] = {nullptr, nullptr}, used[2] = {nullptr, nullptr};
     if (!on_device) {
@@ -284,6 +336,11 @@ extern "C" int rt_trace_columns_chunked(const rt_octree* t, const double* d_src,
     c.hash = d_hash;
     c.st = t->st;
     c.done = done;
+    c.queues = queues;
+    c.qcount = qcount;
+    c.bounds = bounds;
+    c.n_rays = n_rays;
+    c.n_chunks = n_chunks;
     c.batch = a.batch;
     c.layout = a.layout;
     int dev = 0;
@@ -292,12 +349,17 @@ extern "C" int rt_trace_columns_chunked(const rt_octree* t, const double* d_src,
     unsigned long long h_done = 0, last_done = 0, h_segs = 0, last_segs = ~0ull;
     DevStats hst;
     st = RT_OK;
-    if (cudaMemsetAsync(scratch, 0, 256 + rs_bytes, s) != cudaSuccess) st = cuda_error("rt_trace_columns_chunked: state reset");
+    if (cudaMemsetAsync(scratch, 0, head_bytes + rs_bytes, s) != cudaSuccess ||
+        cudaMemcpyAsync(bounds, h_bounds.data(), sizeof(long long) * (n_chunks + 1), cudaMemcpyHostToDevice, s) !=
+            cudaSuccess)
+        st = cuda_error("rt_trace_columns_chunked: state reset");
     for (int sweep = 0; st == RT_OK; sweep++) {
         for (int k = 0; k < n_chunks && st == RT_OK; k++) {
             const int64_t j0 = n * k / n_chunks, j1 = n * (k + 1) / n_chunks;
             c.j0 = j0;
             c.j1 = j1;
+            c.chunk = k;
+            c.fresh = sweep == 0 && k == 0;
             if (on_device) {
                 c.dens = (const char*)dens + (size_t)j0 * n_species * dsz;
             } else {
@@ -320,6 +382,11 @@ extern "C" int rt_trace_columns_chunked(const rt_octree* t, const double* d_src,
                 (mode == RT_MODE_FP64 ? launch_pass<RT_MODE_FP64>(c, grid, s)
                                       : launch_pass<RT_MODE_F32_KAHAN>(c, grid, s)) != cudaSuccess) {
                 st = cuda_error("rt_trace_columns_chunked: pass launch");
+                break;
+            }
+            // queue k has been walked; rays that come back to chunk k join it anew
+            if (cudaMemsetAsync(qcount + k, 0, sizeof(unsigned long long), s) != cudaSuccess) {
+                st = cuda_error("rt_trace_columns_chunked: queue reset");
                 break;
             }
             if (!on_device) cudaEventRecord(used[k & 1], s);
