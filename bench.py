@@ -67,10 +67,12 @@ def peaks():
 
 
 # The sources the bench kernel (the forward trace) is compiled and launched
-# from: its device code, its translation unit and the launch code.
+# from: its device code, its translation unit and the launch code (the
+# launch shape, the ray order and the density check live in rt_api.cu and
+# rt_octree.cu).
 FORWARD_SOURCES = ("paper_2605_09882_gb300/csrc/rt_device.cuh", "paper_2605_09882_gb300/csrc/rt_kernels.cuh",
                    "paper_2605_09882_gb300/csrc/rt_internal.h", "paper_2605_09882_gb300/csrc/rt_forward.cu",
-                   "paper_2605_09882_gb300/csrc/rt_api.cu", "include/rt_api.h")
+                   "paper_2605_09882_gb300/csrc/rt_api.cu", "paper_2605_09882_gb300/csrc/rt_octree.cu")
 
 
 def kernel_source_sha() -> str:

@@ -171,12 +171,14 @@ int prepare_trace(const rt_octree* t, const double* d_src, int64_t n_src, int ns
     return RT_OK;
 }
 
-// Directions per group of the forward's direction-major order: the most
-// whose columns of one source fit in RT_DGROUP_BYTES (a divisor of nd).  At
-// 64 bytes (4 directions of 4 FP32 species) a warp writes whole 64-byte DRAM
-// bursts of every source row it touches, and the rest of the walk keeps its
-// direction-major sweep (measured at 512^3, 4 species: 32 bytes 904.6 ms,
-// 64 bytes 893.9 ms, a whole 192-byte row 901.3 ms per trace).
+// Directions per group of the forward's direction-major order on a uniform
+// cube: the most whose columns of one source fit in RT_DGROUP_BYTES (a divisor
+// of nd).  At 64 bytes (4 directions of 4 FP32 species) a warp writes whole
+// 64-byte DRAM bursts of every source row it touches, and the rest of the
+// walk keeps its direction-major sweep (measured at 512^3, 4 species: 32 bytes
+// 904.6 ms, 64 bytes 893.9 ms, a whole 192-byte row 901.3 ms per trace).  On
+// general octrees the groups were slower (the differentiable workload's
+// forward 12.4 -> 15.0 ms, the 64-cloud batch 1163 -> 1775 ms).
 #ifndef RT_DGROUP_BYTES
 #define RT_DGROUP_BYTES 64
 #endif
@@ -289,7 +291,9 @@ int rt::trace_columns_impl(const rt_octree* t, const double* d_src, int64_t n_sr
         const int cs = check_densities(d_dens, t->dev.n, n_species, a.dens_f64, 0, t->st, s);
         if (cs != RT_OK) return cs;
     }
-    a.dgroup = output_dgroup(a.nd, n_species, mode);
+    // (a general octree keeps one direction per pop: there the direction-major
+    // sweep's L2 reuse of the walk outweighs the output's partial bursts)
+    if (a.t.uniform_level >= 0) a.dgroup = output_dgroup(a.nd, n_species, mode);
     const int fit = occupancy_fwd(0, mode, n_species, a.t.uniform_level >= 0, g_block);
     if (cudaMemsetAsync(&t->st->queue, 0, sizeof(unsigned long long), s) != cudaSuccess)
         return cuda_error("rt_trace_columns: queue reset");
@@ -315,64 +319,6 @@ int rt_trace_paths(const rt_octree* t, const double* d_src, int64_t n_src, int n
         return cuda_error("rt_trace_paths: queue reset");
     if (launch_paths(a, mode, g_block, grid_for(fit), s) != cudaSuccess)
         return cuda_error("rt_trace_paths: launch");
-    return RT_OK;
-}
-
-int rt_trace_columns_adjoint(const rt_octree* t, const double* d_src, int64_t n_src, int nside,
-                             const void* d_grad_out, int n_species, int mode, double* d_grad_dens,
-                             int path_policy, void* stream)
-{
-    TraceArgs a;
-    int st = prepare_trace(t, d_src, n_src, nside, n_species, mode, a, "rt_trace_columns_adjoint");
-    if (st != RT_OK) return st;
-    if (path_policy < 0 || path_policy > 3)
-        return set_error(RT_ERR_ARG, "rt_trace_columns_adjoint: path_policy must be 0, 1, 2 or 3");
-    if (n_src == 0) return RT_OK;
-    if (!d_grad_out || !d_grad_dens) return set_error(RT_ERR_ARG, "rt_trace_columns_adjoint: null gradient pointer");
-    if (!aligned16(d_grad_out) || !aligned16(d_grad_dens))
-        return set_error(RT_ERR_ARG, "rt_trace_columns_adjoint: gradients must be 16-byte aligned");
-    if (path_policy == 2) {
-        rt_paths* p = nullptr;
-        st = rt_record_paths(t, d_src, n_src, nside, mode, stream, &p);
-        if (st != RT_OK) return st;
-        st = rt_paths_adjoint(p, d_grad_out, n_species, d_grad_dens, stream);
-        rt_destroy_paths(p);
-        return st;
-    }
-    a.gin = d_grad_out;
-    a.out = d_grad_dens;
-    cudaStream_t s = (cudaStream_t)stream;
-    if (path_policy == 3) {
-        // deterministic: the leaf gather if the sources have its layout, else
-        // the ordered adjoint over a record of the paths
-        if (gather_applies(t, a)) {
-            st = launch_adjoint_gather((rt_octree*)t, a, mode, s);
-            if (st != RT_OK) return st;
-            int off = 1;
-            if (cudaMemcpyAsync(&off, &t->st->gather_off, sizeof off, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-                cudaStreamSynchronize(s) != cudaSuccess)
-                return cuda_error("rt_trace_columns_adjoint: gather flag readback");
-            if (off == 0) return RT_OK;
-        }
-        rt_paths* p = nullptr;
-        st = rt_record_paths(t, d_src, n_src, nside, mode, stream, &p);
-        if (st != RT_OK) return st;
-        st = rt_paths_adjoint_ordered(p, d_grad_out, n_species, d_grad_dens, stream);
-        rt_destroy_paths(p);
-        return st;
-    }
-    if (path_policy == 0 && gather_applies(t, a)) {
-        // the leaf gather, with the scatter below as the fallback the device
-        // takes when the sources do not have the gather's layout
-        st = launch_adjoint_gather((rt_octree*)t, a, mode, s);
-        if (st != RT_OK) return st;
-        a.gate = &t->st->gather_off;
-    }
-    const int fit = occupancy_adj(mode, n_species, a.t.uniform_level >= 0, g_block);
-    if (cudaMemsetAsync(&t->st->queue, 0, sizeof(unsigned long long), s) != cudaSuccess)
-        return cuda_error("rt_trace_columns_adjoint: queue reset");
-    if (launch_adjoint(a, mode, g_block, grid_for(fit), s) != cudaSuccess)
-        return cuda_error("rt_trace_columns_adjoint: launch");
     return RT_OK;
 }
 
