@@ -157,3 +157,23 @@ def test_gather_accumulates_into_grad(rt):
     acc = rt.trace_columns_adjoint(tree, src, 1, g, "fp64", grad_dens=base.clone())
     torch.testing.assert_close(acc, base + once, rtol=1e-14, atol=0)
     tree.close()
+
+
+@pytest.mark.parametrize("level", [0, 1])
+def test_gather_smallest_cubes(rt, level):
+    """A single leaf (level 0) and a 2^3 cube: the shortest tables, a row of
+    one or two leaves in a 32-lane warp."""
+    rng = np.random.default_rng(980 + level)
+    keys, lev = uniform_octree(level)
+    src_h = _centres(keys, lev)
+    dirs = oracle.healpix(2)
+    g = rng.random((src_h.shape[0], dirs.shape[0], 2))
+    tree = rt.Octree(_dev(keys), _dev(lev))
+    ref = oracle.adjoint(keys, lev, 2, src_h, dirs, g)
+    gd, st = _run(rt, tree, _dev(src_h), 2, _dev(g), "fp64")
+    assert st["gathered"] == 1
+    _bound_check(gd, ref, ref, 1e-12)
+    gk, st = _run(rt, tree, _dev(src_h), 2, _dev(g.astype(np.float32)), "f32k")
+    refk = oracle.adjoint(keys, lev, 2, src_h, dirs, g.astype(np.float32).astype(np.float64))
+    _bound_check(gk, refk, refk, 1e-5)
+    tree.close()

@@ -133,3 +133,20 @@ def test_chunked_amr128(rt, n_chunks):
             assert np.all(np.abs(g - want) <= 1e-5 * np.abs(want) + 1e-30)
         del ref, got, nseg, hsh, nref, href
     tree.close()
+
+
+def test_chunked_empty_and_all_masked(rt):
+    import torch
+    rng = np.random.default_rng(1310)
+    keys, lev, _ = random_octree(rng, 1, 4, 0.4)
+    dens = _dev(rng.uniform(0.1, 2.0, size=(keys.shape[0], 4)).astype(np.float32))
+    tree = rt.Octree(_dev(keys), _dev(lev))
+    none = rt.trace_columns_chunked(tree, _dev(np.zeros((0, 3))), 1, dens, 3, "f32k")
+    assert none.shape == (0, 12, 4)
+    src = _dev(rng.random((50, 3)))
+    got, nseg, hsh = rt.trace_columns_chunked(tree, src, 1, dens, 3, "f32k",
+                                              mask=torch.zeros(50, dtype=torch.uint8, device="cuda"), paths=True)
+    assert torch.count_nonzero(got) == 0 and torch.count_nonzero(nseg) == 0 and torch.count_nonzero(hsh) == 0
+    with pytest.raises(rt.RTError):
+        rt.trace_columns_chunked(tree, src, 1, dens, keys.shape[0] + 1, "f32k")  # more chunks than leaves
+    tree.close()
