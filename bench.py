@@ -83,11 +83,11 @@ def kernel_source_sha() -> str:
     return h.hexdigest()[:16]
 
 
-def kernel_profile():
-    """Per-segment counters of the trace kernel from the committed ncu summary
-    (a 256^3 capture: warp instructions and DRAM bytes per segment), if it was
-    taken from the current kernel sources (else None)."""
-    path = os.path.join(ROOT, "profiles", "trace_f32k_uniform512.json")
+def kernel_profile(name="trace_f32k_uniform512"):
+    """Per-segment counters of a trace kernel from a committed ncu summary
+    (warp instructions and DRAM bytes per segment), if it was taken from the
+    current kernel sources (else None)."""
+    path = os.path.join(ROOT, "profiles", name + ".json")
     try:
         with open(path) as f:
             m = json.load(f)
@@ -269,6 +269,17 @@ def amr_leg(rt, dev, stream, check_sources=400, reps=3, base=128):
     got = out[idx].double().cpu().numpy()
     err = np.abs(got - want) / np.maximum(np.abs(want), 1e-300)
     res["parity_sample"] = {"n_src": int(idx.numel()), "max_rel": float(err.max())}
+    # its bound: instruction issue, warp instructions per segment from the
+    # committed capture of the same kernel on the 64^3-base cloud of this recipe
+    prof = kernel_profile("trace_f32k_amr64")
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak = sms * 4 * 2070e6
+    res["roofline"] = {"bound": "issue", "unit": "warp-instructions/s", "peak": peak,
+                       "peak_kind": f"derived: {sms} SMs x 4 schedulers x 2070 MHz",
+                       "warp_inst_per_segment": prof["warp_inst_per_segment"] if prof else None,
+                       "achieved": segs / t * prof["warp_inst_per_segment"] if prof else None,
+                       "frac": segs / t * prof["warp_inst_per_segment"] / peak if prof else None,
+                       "profile": "profiles/trace_f32k_amr64.md"}
     # Alg. 1's chunked contribution grid: 8 Morton-range chunks, densities
     # streamed from page-locked host memory, rays carried between chunks
     d_host = dens.cpu().pin_memory()
