@@ -93,7 +93,9 @@ def kernel_profile(name="trace_f32k_uniform512"):
             m = json.load(f)
         if m.get("kernel_source_sha") == kernel_source_sha():
             return {"warp_inst_per_segment": float(m["warp_inst_per_segment"]),
-                    "dram_bytes_per_segment": float(m["dram_bytes_per_segment"])}
+                    "dram_bytes_per_segment": float(m["dram_bytes_per_segment"]),
+                    "issue_active_pct": m.get("issue_active_pct"), "lts_hit_pct": m.get("lts_hit_pct"),
+                    "warp_exec_efficiency": m.get("warp_exec_efficiency")}
     except Exception:
         pass
     return None
@@ -182,6 +184,9 @@ def issue_roofline(seg_per_launch, launch_s, clk, hbm_gbs, hbm_kind, dev):
         r["frac"] = r["achieved"] / issue_peak
         r["traffic"] = prof["dram_bytes_per_segment"] * seg_per_launch
         r["dram_frac"] = r["traffic"] / launch_s / (hbm_gbs * 1e9)
+        r["ncu"] = {"issue_active_pct": prof["issue_active_pct"], "lts_hit_pct": prof["lts_hit_pct"],
+                    "warp_exec_efficiency": prof["warp_exec_efficiency"],
+                    "dram_gbs": r["traffic"] / launch_s / 1e9}
     return r
 
 
@@ -279,6 +284,8 @@ def amr_leg(rt, dev, stream, check_sources=400, reps=3, base=128):
                        "warp_inst_per_segment": prof["warp_inst_per_segment"] if prof else None,
                        "achieved": segs / t * prof["warp_inst_per_segment"] if prof else None,
                        "frac": segs / t * prof["warp_inst_per_segment"] / peak if prof else None,
+                       "ncu": {"issue_active_pct": prof["issue_active_pct"], "lts_hit_pct": prof["lts_hit_pct"],
+                               "warp_exec_efficiency": prof["warp_exec_efficiency"]} if prof else None,
                        "profile": "profiles/trace_f32k_amr64.md"}
     # Alg. 1's chunked contribution grid: 8 Morton-range chunks, densities
     # streamed from page-locked host memory, rays carried between chunks
