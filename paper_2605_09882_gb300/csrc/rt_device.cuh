@@ -458,6 +458,23 @@ constexpr float kEA = 0x1p-23f;
 // fractions are all zero (every leaf centre down to level 20): then ph = pl =
 // 0 and A = F - qi is the whole distance.
 
+// (h1 - h0) + (l1 - l0) for the double-float times h + l: both differences
+// in one packed two-lane FP32 subtraction (each lane rounds to nearest, as
+// the two scalar subtractions would).
+__device__ __forceinline__ float diff_sum(float h1, float l1, float h0, float l0)
+{
+    float dh, dl;
+    asm("{\n\t.reg .b64 a, b;\n\t"
+        "mov.b64 a, {%2, %3};\n\t"
+        "mov.b64 b, {%4, %5};\n\t"
+        "sub.rn.f32x2 a, a, b;\n\t"
+        "mov.b64 {%0, %1}, a;\n\t"
+        "}"
+        : "=f"(dh), "=f"(dl)
+        : "f"(h1), "f"(l1), "f"(h0), "f"(l0));
+    return __fadd_rn(dh, dl);
+}
+
 // ------------------------------------ F32-Kahan walk on a uniform grid
 
 // Double-float exit time t = (A - ph - pl) * (ih + il) (depth-21 units) of one
@@ -730,10 +747,9 @@ __device__ __forceinline__ int walk_f32k_grid(const DevTree& t, const DirConst* 
             E = exit_set<VM, QZ, true>(th, Af, qf, ih, flags, cE, dp, bs, wc);
         }
         const float ths = sel3(th, bs), tls = sel3(tl, bs);
-        const float ds = __fadd_rn(__fsub_rn(ths, tih), __fsub_rn(tls, til));
+        const float ds = diff_sum(ths, tls, tih, til);
         tih = ths;
         til = tls;
-        vis.acc(ds);
         wc.nseg++;
         bool leaving = false;
         // A warp whose lanes all take the same locked step (every lane of a
@@ -749,6 +765,9 @@ __device__ __forceinline__ int walk_f32k_grid(const DevTree& t, const DirConst* 
             if ((VM & 2) && (E & 2u)) grid_step<1, QZ, LOCK>(Af, Alim, ph, pl, ih, il, th, tl, dl, fsize, leaving);
             if ((VM & 4) && (E & 4u)) grid_step<2, QZ, LOCK>(Af, Alim, ph, pl, ih, il, th, tl, dl, fsize, leaving);
         }
+        // accumulated after the step, which needs no densities, so that the
+        // step runs while the leaf's densities are still on their way
+        vis.acc(ds);
         if (leaving || wc.nseg >= lim) {  // the cap ends a ray that still goes on
             if (leaving) break;
             return RT_ERR_STEP_LIMIT;

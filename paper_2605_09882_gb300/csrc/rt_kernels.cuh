@@ -31,15 +31,38 @@ namespace rt {
 
 // EX: the densities are known to be FP32 with exactly SM species, so the
 // gather needs no per-segment dtype or count test.
+// One Kahan step for two species at once, in the packed two-lane FP32
+// instructions: y = n*ds + c, t = s + y, c = y - (t - s), s = t, where c is
+// the compensation with its sign flipped and d2 holds ds in both lanes.  Each
+// lane rounds to nearest on its own, and RN(y - u) = -RN(u - y), so the sums
+// are bit for bit those of the scalar form y = n*ds - c', c' = (t - s) - y.
+__device__ __forceinline__ void kahan2(float& s0, float& s1, float& c0, float& c1, float n0, float n1,
+                                       unsigned long long d2)
+{
+    asm("{\n\t.reg .b64 s, c, x, y, t, u;\n\t"
+        "mov.b64 s, {%0, %1};\n\t"
+        "mov.b64 c, {%2, %3};\n\t"
+        "mov.b64 x, {%4, %5};\n\t"
+        "fma.rn.f32x2 y, x, %6, c;\n\t"
+        "add.rn.f32x2 t, s, y;\n\t"
+        "sub.rn.f32x2 u, t, s;\n\t"
+        "sub.rn.f32x2 c, y, u;\n\t"
+        "mov.b64 {%0, %1}, t;\n\t"
+        "mov.b64 {%2, %3}, c;\n\t"
+        "}"
+        : "+f"(s0), "+f"(s1), "+f"(c0), "+f"(c1)
+        : "f"(n0), "f"(n1), "l"(d2));
+}
+
 template <int SM, bool EX = false>
 struct FwdKahan {  // FP32 columns with Kahan compensation
-    float sum[SM], cmp[SM], n[SM];
+    float sum[SM], ncmp[SM], n[SM];  // ncmp: the compensation, negated
     const void* dens;
     int f64, S;
     __device__ __forceinline__ void init()
     {
 #pragma unroll
-        for (int k = 0; k < SM; k++) sum[k] = cmp[k] = 0.f;
+        for (int k = 0; k < SM; k++) sum[k] = ncmp[k] = 0.f;
     }
     __device__ __forceinline__ void pre(uint32_t j)
     {
@@ -50,12 +73,15 @@ struct FwdKahan {  // FP32 columns with Kahan compensation
     __device__ __forceinline__ void acc(F dsin)
     {
         const float ds = (float)dsin;
+        unsigned long long d2 = 0ull;
+        if (SM > 1) asm("mov.b64 %0, {%1, %1};" : "=l"(d2) : "f"(ds));
 #pragma unroll
-        for (int k = 0; k < SM; k++) {
-            const float y = __fmaf_rn(n[k], ds, -cmp[k]);
-            const float tt = __fadd_rn(sum[k], y);
-            cmp[k] = __fsub_rn(__fsub_rn(tt, sum[k]), y);
-            sum[k] = tt;
+        for (int k = 0; k + 1 < SM; k += 2) kahan2(sum[k], sum[k + 1], ncmp[k], ncmp[k + 1], n[k], n[k + 1], d2);
+        if (SM & 1) {
+            const float y = __fmaf_rn(n[SM - 1], ds, ncmp[SM - 1]);
+            const float tt = __fadd_rn(sum[SM - 1], y);
+            ncmp[SM - 1] = __fsub_rn(y, __fsub_rn(tt, sum[SM - 1]));
+            sum[SM - 1] = tt;
         }
     }
     template <class F>
