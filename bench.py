@@ -264,8 +264,8 @@ def amr_leg(rt, dev, stream, check_sources=400, reps=3, base=128):
     res = {"workload": "%d^3 base AMR (2 levels above p90, %d leaves), 4 FP32 species, 1M mass-weighted "
                        "sources, Nside 2, F32-Kahan" % (base, keys.numel()),
            "value": segs / t, "unit": "ray-segments/s", "ms_per_step": t * 1e3,
-           "segments_per_step": int(segs), "exit_fallbacks_per_step": st["exit_fallbacks"] / 4,
-           "lookup_fallbacks_per_step": st["lookup_fallbacks"] / 4}
+           "segments_per_step": int(segs), "exit_fallbacks_per_step": st["exit_fallbacks"] / (reps + 1),
+           "lookup_fallbacks_per_step": st["lookup_fallbacks"] / (reps + 1)}
     import oracle
     idx = torch.arange(0, src.shape[0], src.shape[0] // check_sources, device=dev)[:check_sources]
     want, _, _ = oracle.trace(keys.cpu().numpy().view(np.uint64), lev.cpu().numpy(),

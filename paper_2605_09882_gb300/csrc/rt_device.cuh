@@ -832,11 +832,16 @@ __device__ __forceinline__ long long find_leaf(const DevTree& t, const uint32_t 
         return first;
     }
     if (code <= kDepth) {
-        const int sl = kDepth - code;
-        const uint32_t mask = (1u << (code - t.T)) - 1u;
+        const int sl = kDepth - code, nb = code - t.T;  // nb: bits per axis of the index within the cell
+        const uint32_t mask = (1u << nb) - 1u;
+        level = code;
+        if (nb == 1)  // one level below the table: the octant
+            return first + (long long)(((c[0] >> sl) & 1u) | (((c[1] >> sl) & 1u) << 1) | (((c[2] >> sl) & 1u) << 2));
+        if (nb <= 10)  // the 30-bit interleave suffices
+            return first + (long long)(spread10((c[0] >> sl) & mask) | (spread10((c[1] >> sl) & mask) << 1) |
+                                       (spread10((c[2] >> sl) & mask) << 2));
         const uint64_t local = spread21((c[0] >> sl) & mask) | (spread21((c[1] >> sl) & mask) << 1) |
                                (spread21((c[2] >> sl) & mask) << 2);
-        level = code;
         return first + (long long)local;
     }
     if (code == kCodeHole) return -1;
