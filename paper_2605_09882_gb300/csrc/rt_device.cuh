@@ -148,10 +148,25 @@ __device__ __forceinline__ void leaf_box(uint64_t key, int level, uint32_t lo[3]
 
 // Source coordinate b truncated to the 2^-53 lattice: q = floor(x * 2^53).
 // Returns false for a non-finite value or one outside [0, 1).
+//
+// Taken from the bits of x with integer operations (the FP64 pipe is narrow
+// and every ray needs this for each axis): x = m 2^(e - 1075) for a biased
+// exponent e >= 1 (m with its implicit bit), so x 2^53 = m 2^(e - 1022) and,
+// as x < 1 means e <= 1022, q = m >> (1022 - e).  A subnormal x gives q = 0.
+// Equal to trunc(x * 2^53) in FP64, where the product is exact.
 __device__ __forceinline__ bool fixed_source(double x, long long& q)
 {
-    if (!(x >= 0.0 && x < 1.0)) return false;
-    q = __double2ll_rz(__dmul_rn(x, 0x1p53));
+    const long long bits = __double_as_longlong(x);
+    // [0, 1): sign clear and below the bits of 1.0 (NaN and infinity are
+    // above); -0.0 is the one negative-signed value inside
+    if (bits < 0 || bits >= 0x3FF0000000000000ll) {
+        q = 0;
+        return bits == (long long)0x8000000000000000ull;
+    }
+    const int e = (int)(bits >> 52);
+    const long long m = (bits & 0x000FFFFFFFFFFFFFll) | ((long long)(e != 0) << 52);
+    const int sh = 1022 - e;
+    q = sh >= 53 ? 0ll : (m >> sh);
     return true;
 }
 
@@ -631,10 +646,16 @@ __device__ __forceinline__ int source_fixed(const double* __restrict__ src, cons
         qi[b] = (int)(q >> 32);
         qf[b] = (uint32_t)(q & 0xffffffffll);
         if ((uint32_t)qi[b] >= t.ext[b]) return RT_ERR_SOURCE_OUTSIDE;
+        // fh = qf rounded to a float; qf - fh is below 2^7 in magnitude, so
+        // both are taken without 64-bit conversions: fh is an integer of at
+        // most 33 bits, read back from its exponent and significand
         const float fh = __uint2float_rn(qf[b]);
-        const long long back = (long long)__float2ull_rz(fh);
+        const uint32_t fb = __float_as_uint(fh);
+        const int fe = (int)(fb >> 23) - 150;  // fh = (significand) 2^fe
+        const uint64_t fm = (uint64_t)((fb & 0x7fffffu) | 0x800000u);
+        const long long back = (long long)(fe >= 0 ? fm << fe : fm >> min(-fe, 24));  // fh = 0: 0
         ph[b] = fh * 0x1p-32f;
-        pl[b] = __ll2float_rn((long long)qf[b] - back) * 0x1p-32f;
+        pl[b] = __int2float_rn((int)((long long)qf[b] - back)) * 0x1p-32f;
     }
     return RT_OK;
 }
