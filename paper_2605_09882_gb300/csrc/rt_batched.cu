@@ -52,7 +52,8 @@ __global__ void __launch_bounds__(256, RT_MIN_BLOCKS_BATCHED) k_batched(const Ba
     const bool in_smem = b.n_clouds <= kSmemClouds;
     if (in_smem)
         for (int i = threadIdx.x; i <= b.n_clouds; i += blockDim.x) s_off[i] = b.ray_off[i];
-    __syncthreads();
+    if (MODE == RT_MODE_F32_KAHAN) fill_spread_table();  // its barrier covers s_off too
+    else __syncthreads();
     const unsigned long long* off = in_smem ? s_off : b.ray_off;
     const int lane = threadIdx.x & 31;
     unsigned long long n_rays = 0, n_segs = 0, n_efb = 0, n_lfb = 0;

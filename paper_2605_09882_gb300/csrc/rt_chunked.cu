@@ -114,6 +114,7 @@ template <int MODE, int SM>
 __global__ void __launch_bounds__(256, RT_MIN_BLOCKS_CHUNK) k_chunk_pass(const ChunkArgs a)
 {
     using T = typename std::conditional<MODE == RT_MODE_FP64, double, float>::type;
+    if (MODE == RT_MODE_F32_KAHAN) fill_spread_table();
     const int lane = threadIdx.x & 31;
     const unsigned long long total = a.fresh ? (unsigned long long)(a.layout ? a.n_src : a.n_src_pad) * (unsigned long long)a.nd
                                              : *(volatile unsigned long long*)(a.qcount + a.chunk);

@@ -58,6 +58,19 @@ __device__ __forceinline__ uint32_t spread10(uint32_t v)
 
 constexpr uint32_t kDilX = 0x09249249u;  // bits 3b of a 30-bit Morton index
 
+// spread10 of every 10-bit value, per block in shared memory, for the leaf
+// lookup of the F32-Kahan tree walk (one load per axis instead of the nine
+// instructions of the shifts and masks).  Every kernel that runs that walk
+// fills it first; the lookup masks what it reads to the table's range, so an
+// unfilled table could give a wrong leaf but no out-of-range access.
+__shared__ uint32_t s_spread10[1024];
+
+__device__ __forceinline__ void fill_spread_table()
+{
+    for (int i = threadIdx.x; i < 1024; i += blockDim.x) s_spread10[i] = spread10((uint32_t)i);
+    __syncthreads();
+}
+
 // The bits of a 30-bit Morton index that belong to the two axes other than b.
 __device__ __forceinline__ constexpr uint32_t dil_holes(int b) { return ~(kDilX << b) & 0x3fffffffu; }
 
@@ -844,7 +857,9 @@ __device__ __forceinline__ float small_int_to_float(uint32_t v)
 __device__ __forceinline__ long long find_leaf(const DevTree& t, const uint32_t c[3], int& level)
 {
     const int s = kDepth - t.T;
-    const uint32_t cell = spread10(c[0] >> s) | (spread10(c[1] >> s) << 1) | (spread10(c[2] >> s) << 2);
+    const uint32_t cell = (s_spread10[(c[0] >> s) & 1023u] | (s_spread10[(c[1] >> s) & 1023u] << 1) |
+                           (s_spread10[(c[2] >> s) & 1023u] << 2)) &
+                          ((1u << (3 * t.T)) - 1u);
     const uint64_t e = __ldg(t.table + cell);
     const int code = (int)(e & 63u);
     const long long first = (long long)(e >> 6);
@@ -859,8 +874,9 @@ __device__ __forceinline__ long long find_leaf(const DevTree& t, const uint32_t 
         if (nb == 1)  // one level below the table: the octant
             return first + (long long)(((c[0] >> sl) & 1u) | (((c[1] >> sl) & 1u) << 1) | (((c[2] >> sl) & 1u) << 2));
         if (nb <= 10)  // the 30-bit interleave suffices
-            return first + (long long)(spread10((c[0] >> sl) & mask) | (spread10((c[1] >> sl) & mask) << 1) |
-                                       (spread10((c[2] >> sl) & mask) << 2));
+            return first + (long long)((s_spread10[(c[0] >> sl) & mask] | (s_spread10[(c[1] >> sl) & mask] << 1) |
+                                        (s_spread10[(c[2] >> sl) & mask] << 2)) &
+                                       ((1u << (3 * nb)) - 1u));
         const uint64_t local = spread21((c[0] >> sl) & mask) | (spread21((c[1] >> sl) & mask) << 1) |
                                (spread21((c[2] >> sl) & mask) << 2);
         return first + (long long)local;

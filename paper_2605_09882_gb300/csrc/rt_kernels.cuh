@@ -240,6 +240,7 @@ __global__ void __launch_bounds__(256, (MODE == RT_MODE_F32_KAHAN) ? (UNIFORM ? 
 k_trace(const TraceArgs a)
 {
     if (KIND == 2 && a.gate && *(volatile const int*)a.gate == 0) return;  // the leaf gather ran instead
+    if (MODE == RT_MODE_F32_KAHAN && !UNIFORM) fill_spread_table();
     const int lane = threadIdx.x & 31;
     const unsigned long long total = (unsigned long long)(a.layout ? a.n_src : a.n_src_pad) * (unsigned long long)a.nd;
     const long long cap = a.t.step_cap;
