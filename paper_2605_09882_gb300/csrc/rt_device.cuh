@@ -845,12 +845,6 @@ __device__ __forceinline__ int floor_small(float v)
     return __float_as_int(__fadd_rd(v, 12582912.0f)) - 0x4B400000;
 }
 
-// Exact float of an integer 0 <= v < 2^23 without a conversion instruction.
-__device__ __forceinline__ float small_int_to_float(uint32_t v)
-{
-    return __fsub_rn(__int_as_float(0x4B000000 | (int)v), 8388608.0f);
-}
-
 // Leaf containing the depth-21 point c, and its level.  The coarse table gives
 // the leaf directly for a coarse cell inside one leaf or of one level (no key
 // or level is read then); a mixed cell is searched by key.  -1: no leaf.
@@ -912,7 +906,7 @@ __device__ __forceinline__ int walk_f32k_tree(const DevTree& t, const DirConst* 
     // table where they are used: one broadcast load per warp, kept out of the
     // per-ray registers.
     const int flags = __ldg(&dp->flags);
-    float ph[3], pl[3], qif[3];
+    float ph[3], pl[3], qif[3];  // qif: 2^23 + qi, exact
     int qi[3];
     uint32_t qf[3], c[3];
     float cE = 0.f;
@@ -920,7 +914,7 @@ __device__ __forceinline__ int walk_f32k_tree(const DevTree& t, const DirConst* 
     if (st != RT_OK) return st;
 #pragma unroll
     for (int b = 0; b < 3; b++) {
-        qif[b] = small_int_to_float((uint32_t)qi[b]);
+        qif[b] = __int_as_float(0x4B000000 | qi[b]);
         c[b] = (uint32_t)qi[b];
         if (VM & (1 << b)) cE = fmaxf(cE, fabsf(dir_const(&dp->ih[b])) * kEA);
     }
@@ -964,7 +958,8 @@ __device__ __forceinline__ int walk_f32k_tree(const DevTree& t, const DirConst* 
             if (VM & (1 << b)) {
                 ih[b] = dir_const(&dp->ih[b]);
                 const uint32_t F = ((flags >> (3 + b)) & 1) ? lo[b] + size : lo[b];
-                Af[b] = __fsub_rn(small_int_to_float(F), qif[b]);
+                // (2^23 + F) - (2^23 + qi) = F - qi: integers below 2^24, exact
+                Af[b] = __fsub_rn(__int_as_float(0x4B000000 | (int)F), qif[b]);
                 if (QZ) {
                     th[b] = __fmul_rn(Af[b], ih[b]);
                 } else {
