@@ -156,7 +156,9 @@ def test_source_outside_sets_status_and_zeros(rt):
     keys, lev = uniform_octree(3)
     tree = rt.Octree(_dev(keys), _dev(lev))
     dens = torch.ones((keys.shape[0], 1), dtype=torch.float32, device="cuda")
-    src = torch.tensor([[0.5, 0.5, 0.5], [1.0, 0.5, 0.5], [0.2, float("nan"), 0.1]],
+    src = torch.tensor([[0.5, 0.5, 0.5], [1.0, 0.5, 0.5], [0.2, float("nan"), 0.1],
+                        [0.3, 0.3, -5e-324], [float("inf"), 0.1, 0.1], [0.1, -float("inf"), 0.1],
+                        [0.1, 0.1, float(np.nextafter(1.0, 2.0))], [-1e-300, 0.5, 0.5]],
                        dtype=torch.float64, device="cuda")
     for mode in ("f32k", "fp64"):
         tree.reset_stats()
@@ -231,6 +233,29 @@ def test_few_sources_many_directions(rt):
     cloud = synth.uniform_cloud(5, 1.0, 4, fracs=(1.0,), dtype=np.float64)
     _check_case(rt, cloud.keys, cloud.levels, cloud.dens, np.array([[0.515625, 0.515625, 0.515625]]), 16,
                 label="uniform centre nside16")
+
+
+def test_extreme_source_coordinates(rt):
+    """Source coordinates at the ends of what [0, 1) holds, combined per axis:
+    -0.0, the smallest subnormal and the smallest normal double, values below
+    and at the 2^-53 lattice spacing, the largest doubles below 0.5 and below
+    1, and points 1 to 255 lattice steps below a depth-21 cell face (where the
+    32-bit fraction's FP32 rounding goes up to 2^32).  Uniform grid (grid
+    walks) and a random octree (tree walks), Nside 2, both modes."""
+    face = 6 * 2.0 ** -21
+    vals = np.array([-0.0, 0.0, 5e-324, 2.2250738585072014e-308, 2.0 ** -60, 2.0 ** -53, 3 * 2.0 ** -54,
+                     np.nextafter(0.5, 0.0), 0.5, np.nextafter(1.0, 0.0), 0.25 + 2.0 ** -53,
+                     face - 2.0 ** -53, face - 127 * 2.0 ** -53, face - 128 * 2.0 ** -53,
+                     face - 129 * 2.0 ** -53, face - 255 * 2.0 ** -53, 0.75 - 2.0 ** -40])
+    rng = np.random.default_rng(4242)
+    src = np.concatenate([vals[rng.integers(0, len(vals), size=(240, 3))], np.repeat(vals[:, None], 3, axis=1)])
+    assert np.signbit(src).any()  # -0.0 survives the construction
+    keys, lev = uniform_octree(4)
+    dens = rng.uniform(0.1, 10.0, size=(keys.shape[0], 2)).astype(np.float32)
+    _check_case(rt, keys, lev, dens, src, 2, label="uniform16 extreme sources")
+    keys, lev, _ = random_octree(rng, 1, 6, 0.35)
+    dens = rng.uniform(0.1, 10.0, size=(keys.shape[0], 2)).astype(np.float32)
+    _check_case(rt, keys, lev, dens, src, 2, label="octree extreme sources")
 
 
 @pytest.mark.parametrize("seed", range(2))
