@@ -375,8 +375,8 @@ int rt_octree_info(const rt_octree* tree, int64_t* n_leaves, int* max_level, int
  * All scratch (work-queue counter, statistics, status word, direction table)
  * lives in one file-scope device array of about 74 KiB that every GPU which
  * loads the library holds until exit.  The first call on a device looks up
- * that array's address with cudaGetSymbolAddress; make that first call
- * before any stream capture.  Every call reuses the array and re-zeroes the
+ * that array's address with cudaGetSymbolAddress (a runtime call that
+ * allocates nothing).  Every call reuses the array and re-zeroes the
  * counters it needs, so calls that overlap on the GPU (on different streams
  * or threads) race and must be ordered by the caller. */
 int rt_trace_columns_noalloc(const uint64_t* d_keys, const uint8_t* d_levels, int64_t n_leaves,
