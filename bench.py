@@ -176,7 +176,7 @@ def issue_roofline(seg_per_launch, launch_s, clk, hbm_gbs, hbm_kind, dev):
          "warp_inst_per_segment": None, "dram_frac": None,
          "effective_hbm": {"bytes_per_segment": BYTES_PER_SEGMENT, "achieved": eff, "peak": hbm_gbs, "unit": "GB/s",
                            "frac": eff / hbm_gbs, "peak_kind": hbm_kind},
-         "kernel": "k_trace<fwd, F32K, uniform, S=4>",
+         "kernel": "k_trace_pair<S=4> (F32K forward, uniform cube, two rays per lane)",
          "profile": "profiles/trace_f32k_uniform512.md (256^3 capture, per segment)"}
     if prof is not None:
         r["warp_inst_per_segment"] = prof["warp_inst_per_segment"]

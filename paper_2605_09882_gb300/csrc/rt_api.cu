@@ -294,7 +294,13 @@ int rt::trace_columns_impl(const rt_octree* t, const double* d_src, int64_t n_sr
     // (a general octree keeps one direction per pop: there the direction-major
     // sweep's L2 reuse of the walk outweighs the output's partial bursts)
     if (a.t.uniform_level >= 0) a.dgroup = output_dgroup(a.nd, n_species, mode);
-    const int fit = occupancy_fwd(0, mode, n_species, a.t.uniform_level >= 0, g_block);
+    // leaf centres of a uniform cube share their exit sequences: two rays per
+    // lane (FP32 densities with 1, 2, 4 or 8 species, direction-major order)
+    a.pair = mode == RT_MODE_F32_KAHAN && a.t.uniform_level >= 0 && a.layout == 0 && !a.dens_f64 &&
+             (n_species == 1 || n_species == 2 || n_species == 4 || n_species == 8);
+    if (a.pair) a.n_src_pad = (n_src + 63) / 64 * 64;
+    const int fit = a.pair ? occupancy_pair(n_species, g_block)
+                           : occupancy_fwd(0, mode, n_species, a.t.uniform_level >= 0, g_block);
     if (cudaMemsetAsync(&t->st->queue, 0, sizeof(unsigned long long), s) != cudaSuccess)
         return cuda_error("rt_trace_columns: queue reset");
     if (launch_forward(a, mode, g_block, grid_for(fit), s) != cudaSuccess)

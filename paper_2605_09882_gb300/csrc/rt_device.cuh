@@ -811,6 +811,154 @@ __device__ __forceinline__ int walk_f32k_grid(const DevTree& t, const DirConst* 
     return RT_OK;
 }
 
+// ------------------------------------ two rays per lane on a uniform grid
+
+// Two rays of one direction from sources on the depth-21 lattice (zero 32-bit
+// fractions) whose distances to their cells' far faces are equal on every
+// moving axis -- every two leaf centres of a uniform cube -- have the same
+// exit times, exit choices and segment lengths, step for step: each path is
+// the other translated by whole cells.  One lane walks both and takes each
+// exit decision once; the leaf indices, the domain-exit tests, the densities
+// and the sums are per ray.  Each ray's leaves, segment lengths and sums are
+// bit for bit those of walk_f32k_grid.  kNoPair (nothing done): the sources
+// do not qualify.
+constexpr int kNoPair = -3;
+
+template <int b, bool LOCK>
+__device__ __forceinline__ void pair_step(float Af[3], const float Alim0[3], const float Alim1[3],
+                                          const float ih[3], const float il[3], float th[3], float tl[3],
+                                          uint32_t dl0[3], uint32_t dl1[3], float fsize, bool& lv0, bool& lv1)
+{
+    if (LOCK && b == 1) {  // y tracks x (stepped just before)
+        lv0 |= Af[0] == Alim0[1];
+        lv1 |= Af[0] == Alim1[1];
+    } else {
+        lv0 |= Af[b] == Alim0[b];
+        lv1 |= Af[b] == Alim1[b];
+        Af[b] = __fadd_rn(Af[b], fsize);
+        exit_time<true>(Af[b], 0.f, 0.f, ih[b], il[b], th[b], tl[b]);
+    }
+    dl0[b] = (dl0[b] + (1u << b)) | dil_holes(b);
+    dl1[b] = (dl1[b] + (1u << b)) | dil_holes(b);
+}
+
+template <int VM, bool LOCK, class V>
+__device__ __forceinline__ int walk_f32k_grid_pair(const DevTree& t, const DirConst* __restrict__ dp,
+                                                   const double* __restrict__ src0,
+                                                   const double* __restrict__ src1, long long cap, V& v0,
+                                                   V& v1, WalkCounters& w0, WalkCounters& w1, int& st1)
+{
+    const int sh = kDepth - t.uniform_level;
+    const int N1 = (1 << t.uniform_level) - 1;
+    const float fsize = (float)(1 << sh);
+    const int flags = __ldg(&dp->flags);
+    int q0[3], q1[3];
+    uint32_t qf[3], qf1[3];
+    float ph[3], pl[3];
+    if (source_fixed(src0, t, q0, qf, ph, pl) != RT_OK || source_fixed(src1, t, q1, qf1, ph, pl) != RT_OK)
+        return kNoPair;
+    if ((qf[0] | qf[1] | qf[2] | qf1[0] | qf1[1] | qf1[2]) != 0u) return kNoPair;
+    uint32_t dl0[3], dl1[3], xm = 0u;
+    float Af[3], Alim0[3], Alim1[3], th[3], tl[3], ih[3], il[3];
+    float cE = 0.f;
+#pragma unroll
+    for (int b = 0; b < 3; b++) {
+        const int c0 = q0[b] >> sh, c1 = q1[b] >> sh;
+        const bool neg = (VM & (1 << b)) && !((flags >> (3 + b)) & 1);
+        dl0[b] = (spread10((uint32_t)(neg ? (c0 ^ N1) : c0)) << b) | dil_holes(b);
+        dl1[b] = (spread10((uint32_t)(neg ? (c1 ^ N1) : c1)) << b) | dil_holes(b);
+        if (neg) xm |= spread10((uint32_t)N1) << b;
+        Af[b] = Alim0[b] = Alim1[b] = th[b] = tl[b] = ih[b] = il[b] = 0.f;
+        if (VM & (1 << b)) {
+            const int A0 = neg ? q0[b] - (c0 << sh) : ((c0 + 1) << sh) - q0[b];
+            const int A1 = neg ? q1[b] - (c1 << sh) : ((c1 + 1) << sh) - q1[b];
+            if (A0 != A1) return kNoPair;
+            ih[b] = fabsf(__ldg(&dp->ih[b])) * 0x1p-21f;
+            il[b] = (neg ? -__ldg(&dp->il[b]) : __ldg(&dp->il[b])) * 0x1p-21f;
+            Af[b] = __int2float_rn(A0);
+            Alim0[b] = __int2float_rn(neg ? q0[b] : (1 << kDepth) - q0[b]);
+            Alim1[b] = __int2float_rn(neg ? q1[b] : (1 << kDepth) - q1[b]);
+            exit_time<true>(Af[b], 0.f, 0.f, ih[b], il[b], th[b], tl[b]);
+            cE = fmaxf(cE, ih[b] * kEA);
+        }
+    }
+    if (LOCK) {
+        Alim0[1] = __fadd_rn(Alim0[1], fsize);
+        Alim1[1] = __fadd_rn(Alim1[1], fsize);
+    }
+    uint32_t j0 = (dl0[0] & dl0[1] & dl0[2]) ^ xm, j1 = (dl1[0] & dl1[1] & dl1[2]) ^ xm;
+    float tih = 0.f, til = 0.f;
+    const uint32_t capn = (uint32_t)min(cap, (long long)0x7fffffff);  // cap >= 1
+    const uint32_t lim0 = w0.nseg + capn, lim1 = w1.nseg + capn;
+    WalkCounters ws = {0u, 0u, 0u};  // exit fall-backs of the shared decisions so far
+    bool a0 = true, a1 = true;
+    int st0 = RT_OK;
+    st1 = RT_OK;
+    for (;;) {
+        if (a0) v0.pre(j0);
+        if (a1) v1.pre(j1);
+        int bs;
+        unsigned E;
+        if (LOCK) {
+            if (VM == 3) {
+                E = 3u;
+                bs = 0;
+            } else if (__fsub_rn(th[2], th[0]) > (th[2] + th[0]) * kER + 2.f * cE) {
+                E = 3u;
+                bs = 0;
+            } else if (__fsub_rn(th[0], th[2]) > (th[2] + th[0]) * kER + 2.f * cE) {
+                E = 4u;
+                bs = 2;
+            } else {
+                float thl[3] = {th[0], th[0], th[2]}, Afl[3] = {Af[0], Af[0], Af[2]};
+                E = resolve_exit<VM, true>(thl, Afl, qf, ih, flags, dp, th[2] < th[0] ? 2 : 0, ws);
+                bs = __ffs(E) - 1;
+            }
+        } else {
+            E = exit_set<VM, true, true>(th, Af, qf, ih, flags, cE, dp, bs, ws);
+        }
+        const float ths = sel3(th, bs), tls = sel3(tl, bs);
+        const float ds = diff_sum(ths, tls, tih, til);
+        tih = ths;
+        til = tls;
+        bool lv0 = false, lv1 = false;
+        const unsigned am = (LOCK && VM == 7) ? __activemask() : 0u;
+        if (LOCK && VM == 7 && __all_sync(am, E == 4u)) {
+            pair_step<2, LOCK>(Af, Alim0, Alim1, ih, il, th, tl, dl0, dl1, fsize, lv0, lv1);
+        } else if (LOCK && VM == 7 && __all_sync(am, E == 3u)) {
+            pair_step<0, LOCK>(Af, Alim0, Alim1, ih, il, th, tl, dl0, dl1, fsize, lv0, lv1);
+            pair_step<1, LOCK>(Af, Alim0, Alim1, ih, il, th, tl, dl0, dl1, fsize, lv0, lv1);
+        } else {
+            if ((VM & 1) && (E & 1u)) pair_step<0, LOCK>(Af, Alim0, Alim1, ih, il, th, tl, dl0, dl1, fsize, lv0, lv1);
+            if ((VM & 2) && (E & 2u)) pair_step<1, LOCK>(Af, Alim0, Alim1, ih, il, th, tl, dl0, dl1, fsize, lv0, lv1);
+            if ((VM & 4) && (E & 4u)) pair_step<2, LOCK>(Af, Alim0, Alim1, ih, il, th, tl, dl0, dl1, fsize, lv0, lv1);
+        }
+        // each ray is accumulated after the step, as in walk_f32k_grid
+        if (a0) {
+            v0.acc(ds);
+            w0.nseg++;
+            if (lv0 || w0.nseg >= lim0) {  // the cap ends a ray that still goes on
+                a0 = false;
+                st0 = lv0 ? RT_OK : RT_ERR_STEP_LIMIT;
+                w0.exit_fb += ws.exit_fb;
+            }
+        }
+        if (a1) {
+            v1.acc(ds);
+            w1.nseg++;
+            if (lv1 || w1.nseg >= lim1) {
+                a1 = false;
+                st1 = lv1 ? RT_OK : RT_ERR_STEP_LIMIT;
+                w1.exit_fb += ws.exit_fb;
+            }
+        }
+        if (!(a0 || a1)) break;
+        j0 = (dl0[0] & dl0[1] & dl0[2]) ^ xm;
+        j1 = (dl1[0] & dl1[1] & dl1[2]) ^ xm;
+    }
+    return st0;
+}
+
 // True when the x and y exits of a QZ source on a uniform grid stay locked:
 // both axes move, |inv_x| = |inv_y| bitwise, and the source is as far from
 // its leaf's far x face as from its far y face.
@@ -825,6 +973,31 @@ __device__ __forceinline__ bool xy_locked(const DevTree& t, int flags, const dou
     const int ax = ((flags >> 3) & 1) ? size - rx : rx;
     const int ay = ((flags >> 4) & 1) ? size - ry : ry;
     return ax == ay;
+}
+
+// walk_f32k_grid_pair for the direction's moving axes, with the x/y lock when
+// the first source has it (the second, at the same offsets, then has it too).
+template <class V>
+__device__ __forceinline__ int walk_grid_pair(const DevTree& t, const DirConst* __restrict__ dp,
+                                              const double* __restrict__ src0, const double* __restrict__ src1,
+                                              long long cap, V& v0, V& v1, WalkCounters& w0, WalkCounters& w1,
+                                              int& st1)
+{
+    const int flags = __ldg(&dp->flags);
+    const int vm = flags & 7;
+    if ((vm == 3 || vm == 7) && xy_locked(t, flags, src0)) {
+        if (vm == 3) return walk_f32k_grid_pair<3, true>(t, dp, src0, src1, cap, v0, v1, w0, w1, st1);
+        return walk_f32k_grid_pair<7, true>(t, dp, src0, src1, cap, v0, v1, w0, w1, st1);
+    }
+    switch (vm) {
+    case 1: return walk_f32k_grid_pair<1, false>(t, dp, src0, src1, cap, v0, v1, w0, w1, st1);
+    case 2: return walk_f32k_grid_pair<2, false>(t, dp, src0, src1, cap, v0, v1, w0, w1, st1);
+    case 3: return walk_f32k_grid_pair<3, false>(t, dp, src0, src1, cap, v0, v1, w0, w1, st1);
+    case 4: return walk_f32k_grid_pair<4, false>(t, dp, src0, src1, cap, v0, v1, w0, w1, st1);
+    case 5: return walk_f32k_grid_pair<5, false>(t, dp, src0, src1, cap, v0, v1, w0, w1, st1);
+    case 6: return walk_f32k_grid_pair<6, false>(t, dp, src0, src1, cap, v0, v1, w0, w1, st1);
+    default: return walk_f32k_grid_pair<7, false>(t, dp, src0, src1, cap, v0, v1, w0, w1, st1);
+    }
 }
 
 // ------------------------------------ F32-Kahan walk on a general octree

@@ -29,6 +29,16 @@ static cudaError_t dispatch(const TraceArgs& a, int mode, int block, int grid, c
 
 cudaError_t launch_forward(const TraceArgs& a, int mode, int block, int grid, cudaStream_t s)
 {
+    if (a.pair) {
+        switch (a.S) {
+        case 1: k_trace_pair<1><<<grid, block, 0, s>>>(a); break;
+        case 2: k_trace_pair<2><<<grid, block, 0, s>>>(a); break;
+        case 4: k_trace_pair<4><<<grid, block, 0, s>>>(a); break;
+        case 8: k_trace_pair<8><<<grid, block, 0, s>>>(a); break;
+        default: return cudaErrorInvalidValue;
+        }
+        return cudaGetLastError();
+    }
     return dispatch<0>(a, mode, block, grid, s);
 }
 
@@ -64,6 +74,16 @@ static int occ_kind(int mode, int S, bool u, int block)
 int occupancy_fwd(int kind, int mode, int S, bool uniform, int block)
 {
     return kind == 0 ? occ_kind<0>(mode, S, uniform, block) : occ_kind<1>(mode, S, uniform, block);
+}
+
+int occupancy_pair(int S, int block)
+{
+    int n = 0;
+    if (S == 1) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_trace_pair<1>, block, 0);
+    else if (S == 2) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_trace_pair<2>, block, 0);
+    else if (S == 4) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_trace_pair<4>, block, 0);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_trace_pair<8>, block, 0);
+    return n;
 }
 
 }  // namespace rt

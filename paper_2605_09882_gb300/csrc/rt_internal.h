@@ -71,6 +71,7 @@ struct TraceArgs {
     int batch;               // 32-ray groups per queue pop
     int layout;              // ray order: 0 direction-major (sources padded to 32), 1 source-major
     int dgroup;              // layout 0: directions per group (a power of two dividing nd; <= 1: one)
+    int pair;                // forward on a uniform cube: two rays per lane (k_trace_pair); n_src_pad % 64 == 0
     // path recording (KIND 3): per 32-ray group, segment k of lane i is entry
     // rec_off[g] + 32 k + i of rec_leaf / rec_ds
     const long long* rec_off;
@@ -98,6 +99,7 @@ cudaError_t launch_adjoint(const TraceArgs& a, int mode, int block, int grid, cu
 cudaError_t launch_epilogue(const TraceArgs& a, int mode, int block, int grid, cudaStream_t s);
 int occupancy_epi(int mode, int S, bool uniform, int block);
 int occupancy_fwd(int kind, int mode, int S, bool uniform, int block);
+int occupancy_pair(int S, int block);
 int occupancy_adj(int mode, int S, bool uniform, int block);
 
 }  // namespace rt

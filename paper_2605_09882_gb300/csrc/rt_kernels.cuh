@@ -345,4 +345,81 @@ k_trace(const TraceArgs a)
     flush_counters(a.st, n_rays, n_segs, n_efb, n_lfb);
 }
 
+// Forward columns with two rays per lane (walk_grid_pair): F32-Kahan on a
+// uniform cube with FP32 densities of exactly SM species.  A warp pops one
+// unit, a 64-source block and one group of dgroup directions, in the order of
+// k_trace's direction groups; lane i walks sources 64u + i and 64u + 32 + i
+// together for each direction of the group, and one at a time where the two
+// do not qualify.
+#ifndef RT_MIN_BLOCKS_PAIR
+#define RT_MIN_BLOCKS_PAIR 3  // 80 registers: two rays' state without spilling the loop
+#endif
+template <int SM>
+__device__ __forceinline__ void store_cols(const TraceArgs& a, long long ray, const FwdKahan<SM, true>& v)
+{
+    float* o = (float*)a.out + (size_t)ray * SM;
+    if (SM == 4) {
+        *(float4*)o = make_float4(v.sum[0], v.sum[1], v.sum[2], v.sum[3]);
+    } else {
+#pragma unroll
+        for (int k = 0; k < SM; k++) o[k] = v.sum[k];
+    }
+}
+
+template <int SM>
+__global__ void __launch_bounds__(256, RT_MIN_BLOCKS_PAIR) k_trace_pair(const TraceArgs a)
+{
+    const int lane = threadIdx.x & 31;
+    const int D = a.dgroup > 1 ? a.dgroup : 1;
+    const unsigned long long nb2 = (unsigned long long)a.n_src_pad >> 6;
+    const unsigned long long units = nb2 * (unsigned long long)(a.nd / D);
+    const long long cap = a.t.step_cap;
+    unsigned long long n_rays = 0, n_segs = 0, n_efb = 0, n_lfb = 0;
+    for (;;) {
+        unsigned long long u = 0;
+        if (lane == 0) u = atomicAdd(&a.st->queue, 1ull);
+        u = __shfl_sync(RT_FULL, u, 0);
+        if (u >= units) break;
+        const unsigned long long gg = u / nb2, bp = u - gg * nb2;
+        const long long s0 = (long long)(bp << 6) + lane, s1 = s0 + 32;
+        if (s0 >= a.n_src) continue;
+        const bool two = s1 < a.n_src;
+        for (int dd = 0; dd < D; dd++) {
+            const int q = (int)gg * D + dd;
+            const DirConst* d = a.dirs + q;
+            const long long ray0 = s0 * a.nd + q, ray1 = s1 * a.nd + q;
+            WalkCounters w0 = {0u, 0u, 0u}, w1 = {0u, 0u, 0u};
+            FwdKahan<SM, true> v0, v1;
+            v0.dens = v1.dens = a.dens;
+            v0.f64 = v1.f64 = 0;
+            v0.S = v1.S = SM;
+            v0.init();
+            v1.init();
+            int st1 = RT_OK;
+            const int st0 = two ? walk_grid_pair(a.t, d, a.src + 3 * s0, a.src + 3 * s1, cap, v0, v1, w0, w1, st1)
+                                : kNoPair;
+            if (st0 == kNoPair) {
+                forward_ray<RT_MODE_F32_KAHAN, true, SM, true>(a, d, a.src + 3 * s0, cap, ray0, w0);
+                if (two) forward_ray<RT_MODE_F32_KAHAN, true, SM, true>(a, d, a.src + 3 * s1, cap, ray1, w1);
+            } else {
+                if (st0 != RT_OK) {
+                    report_fault(a.st, st0, ray0);
+                    v0.init();
+                }
+                if (st1 != RT_OK) {
+                    report_fault(a.st, st1, ray1);
+                    v1.init();
+                }
+                store_cols<SM>(a, ray0, v0);
+                store_cols<SM>(a, ray1, v1);
+            }
+            n_rays += two ? 2 : 1;
+            n_segs += w0.nseg + w1.nseg;
+            n_efb += w0.exit_fb + w1.exit_fb;
+            n_lfb += w0.lookup_fb + w1.lookup_fb;
+        }
+    }
+    flush_counters(a.st, n_rays, n_segs, n_efb, n_lfb);
+}
+
 }  // namespace rt

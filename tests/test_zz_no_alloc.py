@@ -90,6 +90,32 @@ def test_noalloc_matches_handle_entry_point_uniform(rt):
     _compare(rt, cloud.keys, cloud.levels, cloud.dens, synth.leaf_centres(cloud), 1)
 
 
+def test_paired_and_single_walks_are_bitwise_equal(rt):
+    """On a uniform cube with FP32 densities the handle call walks two rays
+    per lane (leaf centres share their exit sequences) and the allocation-free
+    call one: their F32-Kahan columns and segment counts must be bitwise
+    equal.  Sources: leaf centres (pairs), off-lattice points (single walks),
+    the two interleaved so that pairs mix, and a count that leaves a ragged
+    64-source block; 1, 2, 4 and 8 species."""
+    import torch
+    rng = np.random.default_rng(811)
+    for S in (1, 2, 4, 8):
+        cloud = synth.uniform_cloud(4, 2.0, 12 + S, fracs=tuple(np.linspace(1.0, 0.3, S)), dtype=np.float32)
+        centres = synth.leaf_centres(cloud)
+        off = rng.random((centres.shape[0], 3))
+        mixed = np.where(rng.random((centres.shape[0], 1)) < 0.5, centres, off)
+        src = np.concatenate([centres[:1000], off[:200], mixed[:500], centres[1000:1037]])
+        keys, lev, dens, s_d = _dev(cloud.keys), _dev(cloud.levels), _dev(cloud.dens), _dev(src)
+        tree = rt.Octree(keys, lev)
+        tree.reset_stats()
+        ref = rt.trace_columns(tree, s_d, 2, dens, rt.MODE_F32_KAHAN).cpu().numpy()
+        ref_segs = tree.stats()["segments"]
+        got, segs = _noalloc(rt, keys, lev, int(cloud.levels.max()), s_d, 2, dens, rt.MODE_F32_KAHAN)
+        assert segs == ref_segs, S
+        np.testing.assert_array_equal(got, ref, err_msg=f"S={S}")
+        tree.close()
+
+
 def test_noalloc_largest_direction_table(rt):
     """nside 8, the largest table the fixed scratch holds (768 directions), on a
     small AMR tree."""
