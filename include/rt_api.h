@@ -99,7 +99,7 @@ typedef struct rt_stats {
  * Checks the octree on the device (sorted, aligned, tiling the box; fault
  * precedence ARG > MISALIGNED > UNSORTED > OVERLAP_OR_GAP), builds a coarse
  * Morton table over the top levels and synchronizes `stream` once to read the
- * verdict.  The handle owns the table and a small scratch block. */
+ * validation result.  The handle owns the table and a small scratch block. */
 int rt_build_octree(const uint64_t* d_keys, const uint8_t* d_levels, int64_t n_leaves,
                     const int32_t* h_extent, void* stream, rt_octree** out);
 
