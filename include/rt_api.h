@@ -336,7 +336,11 @@ int rt_set_step_cap(rt_octree* tree, int64_t cap);
 /* Launch shape of the persistent trace kernels: threads per block (a
  * multiple of 32 in 32..256; 0 = default 256), resident blocks per SM (0 =
  * as many as fit) and 32-ray groups a warp takes per work-queue pop (1..64;
- * 0 = default 4).  Applies to later calls in this process. */
+ * 0 = default 4).  Applies to later calls in this process.  The F32-Kahan
+ * forward of rt_trace_columns on a full cube of equal-level leaves with FP32
+ * densities of 1, 2, 4 or 8 species walks two rays per lane: its warps pop
+ * one 64-source block and one direction group at a time, whatever
+ * groups_per_pop says, and at most 3 of its blocks fit on an SM. */
 int rt_set_launch(int threads_per_block, int blocks_per_sm, int groups_per_pop);
 
 /* Caps the coarse-table level of later rt_build_octree calls (-1, the
@@ -369,7 +373,8 @@ int rt_octree_info(const rt_octree* tree, int64_t* n_leaves, int* max_level, int
  *   h_stats: NULL, or host memory that receives this call's statistics and
  *     status; then the call synchronizes `stream`.
  * The launch shape (rt_set_launch) and the ray order are those of
- * rt_trace_columns.  Each call zeroes the statistics and copies the lookup
+ * rt_trace_columns's one-ray-per-lane kernel (where rt_trace_columns walks
+ * two rays per lane, the columns are bitwise the same).  Each call zeroes the statistics and copies the lookup
  * entry and the direction table from host tables that are computed once per
  * nside and never change afterwards.
  * All scratch (work-queue counter, statistics, status word, direction table)
