@@ -185,6 +185,35 @@ def test_step_cap_stops_rays_with_status(rt):
     tree.close()
 
 
+def test_step_cap_on_paired_rays(rt):
+    """The step cap on the two-rays-per-lane walk: leaf centres of a uniform
+    cube (paired), in a full and a ragged 64-source block, with a cap shorter
+    than some rays, so that one ray of a pair stops while the other goes on.
+    A ray within the cap keeps its columns bit for bit, a longer one stops at
+    the cap with zero columns and the step-limit status, and the segment count
+    is the sum of min(path length, cap)."""
+    keys, lev = uniform_octree(4)
+    rng = np.random.default_rng(77)
+    dens = rng.uniform(0.1, 10.0, size=(keys.shape[0], 4)).astype(np.float32)
+    src = synth.leaf_centres(synth.Cloud(keys, lev, np.zeros((keys.shape[0], 1)), (1 << 21,) * 3))[:100]
+    _, _, n_or = oracle.trace(keys, lev, dens.astype(np.float64), src, oracle.healpix(1))
+    cap = 6
+    short = n_or <= cap
+    assert short.any() and (~short).any()
+    tree = rt.Octree(_dev(keys), _dev(lev))
+    d_d, s_d = _dev(dens), _dev(src)
+    full = rt.trace_columns(tree, s_d, 1, d_d, "f32k").cpu().numpy()
+    tree.set_step_cap(cap)
+    tree.reset_stats()
+    capped = rt.trace_columns(tree, s_d, 1, d_d, "f32k").cpu().numpy()
+    st = tree.stats()
+    assert st["status"] == 6, st
+    assert st["segments"] == int(np.minimum(n_or, cap).sum()), st
+    np.testing.assert_array_equal(capped[short], full[short])
+    assert np.all(capped[~short] == 0)
+    tree.close()
+
+
 def test_invalid_octrees_match_oracle_codes(rt):
     rng = np.random.default_rng(3)
     keys, lev, _ = random_octree(rng, 1, 4, 0.4)

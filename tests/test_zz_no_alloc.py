@@ -41,7 +41,7 @@ def _dev(a):
     return torch.from_numpy(a).cuda()
 
 
-def _noalloc(rt, keys, lev, max_level, src, nside, dens, mode, extent=None):
+def _noalloc(rt, keys, lev, max_level, src, nside, dens, mode, extent=None, stats=False):
     import torch
     nd = 12 * nside * nside
     S = dens.shape[1]
@@ -55,7 +55,7 @@ def _noalloc(rt, keys, lev, max_level, src, nside, dens, mode, extent=None):
         out.data_ptr(), C.byref(st), C.c_void_p(torch.cuda.current_stream().cuda_stream))
     assert code == 0, rt._lib.rt_last_error()
     assert st.status == 0 and st.rays == src.shape[0] * nd
-    return out.cpu().numpy(), st.segments
+    return out.cpu().numpy(), (st if stats else st.segments)
 
 
 def _compare(rt, keys_h, lev_h, dens_h, src_h, nside, extent=None):
@@ -109,9 +109,9 @@ def test_paired_and_single_walks_are_bitwise_equal(rt):
         tree = rt.Octree(keys, lev)
         tree.reset_stats()
         ref = rt.trace_columns(tree, s_d, 2, dens, rt.MODE_F32_KAHAN).cpu().numpy()
-        ref_segs = tree.stats()["segments"]
-        got, segs = _noalloc(rt, keys, lev, int(cloud.levels.max()), s_d, 2, dens, rt.MODE_F32_KAHAN)
-        assert segs == ref_segs, S
+        ref_st = tree.stats()
+        got, st = _noalloc(rt, keys, lev, int(cloud.levels.max()), s_d, 2, dens, rt.MODE_F32_KAHAN, stats=True)
+        assert (st.segments, st.exit_fallbacks) == (ref_st["segments"], ref_st["exit_fallbacks"]), S
         np.testing.assert_array_equal(got, ref, err_msg=f"S={S}")
         tree.close()
 
